@@ -1,0 +1,434 @@
+"""Benchmark: direction-optimising BFS throughput (GTEPS) on R-MAT, with the
+HBM-roofline fraction of the traversal kernel, an end-to-end number through
+the public API, the CPU oracle as baseline, and SSSP / CC / PageRank timings
+on the same graph.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--workload rmat22]
+    python bench.py --impl reference ...      # the CPU oracle as reference arm
+
+One step = one traversal from each of the workload's seeded sources (16 by
+default), on a graph that stays resident in HBM.  L2 is flushed before every
+traversal (outside the timed events).  Multi-GPU runs are independent
+replicas (the method does not shard here): each rank owns a full copy of the
+graph, value = edges traversed by all ranks / max-over-ranks time.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "BFS GTEPS & HBM-roofline % at R-MAT 22/26; batched-query p50/p99 latency"
+RMAT_CONFIGS = {
+    "rmat16": dict(scale=16, edge_factor=16, seed=16, wmax=64, weight_seed=116),
+    "rmat22": dict(scale=22, edge_factor=16, seed=22, wmax=64, weight_seed=122),
+    "rmat26": dict(scale=26, edge_factor=16, seed=26, wmax=64, weight_seed=126),
+}
+N_SOURCES = 16
+SOURCE_SEED = 1
+
+
+def _peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            p = json.load(f)
+        return float(p["hbm_gbs"]), "measured"
+    except Exception:
+        return 6800.0, "fallback"
+
+
+# ---------------------------------------------------------------------------
+# Algorithmic byte model (frozen): every element the method must touch, once,
+# at its natural width.  o = offset width.  Edges the method skips (pull early
+# exit, direction switching) are not counted.
+#   push level:  |Q| (2o + 4 + 4 + 4) + E_exam (4 + 4)
+#   pull level:  V_scanned (2o + 4) + E_exam (4 + 4) + V_new (4 + 4) + V/8
+# ---------------------------------------------------------------------------
+def bfs_bytes(stats: dict, nv: int, off_bytes: int) -> int:
+    total = 0
+    for lv in range(stats["levels"]):
+        q = stats["frontier"][lv]
+        ex = stats["edges_examined"][lv]
+        if stats["dir"][lv] == 0:
+            total += q * (2 * off_bytes + 12) + ex * 8
+        else:
+            vs = stats["vertices_scanned"][lv]
+            new = stats["discovered"][lv]
+            total += vs * (2 * off_bytes + 4) + ex * 8 + new * 8 + nv // 8
+    return total
+
+
+def sssp_bytes(stats: dict, off_bytes: int) -> int:
+    # per round: |Q| (2o + 4 + 4) + E_exam (4 + 4 + 8)
+    return sum(stats["frontier"][r] * (2 * off_bytes + 8) + stats["edges_examined"][r] * 16
+               for r in range(stats["levels"]))
+
+
+def pr_bytes(nv: int, ne: int, off_bytes: int, iters: int) -> int:
+    return iters * (nv * (off_bytes + 12) + ne * 8)
+
+
+def cc_bytes(nv: int, ne: int, off_bytes: int, rounds: int) -> int:
+    return rounds * (ne * 12 + nv * (off_bytes + 4)) + max(rounds - 1, 0) * nv * 8
+
+
+# ---------------------------------------------------------------------------
+class ClockSampler:
+    """nvidia-smi clock/throttle samples while the timed region runs."""
+
+    FIELDS = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int, period_ms: int = 50):
+        self.proc = None
+        self.lines = []
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(gpu_index), f"--query-gpu={self.FIELDS}",
+                 "--format=csv,noheader,nounits", "-lms", str(period_ms)],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.thread = threading.Thread(target=self._read, daemon=True)
+            self.thread.start()
+        except Exception:
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append((time.time(), line.strip()))
+
+    def stop(self, t0: float, t1: float) -> dict:
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        samples = [l for t, l in self.lines if t0 - 0.05 <= t <= t1 + 0.05] or \
+                  [l for _, l in self.lines]
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for s in samples:
+            parts = [p.strip() for p in s.split(",")]
+            if len(parts) < 8:
+                continue
+            try:
+                sm.append(float(parts[0]))
+                smax.append(float(parts[1]))
+            except ValueError:
+                continue
+            for n, p in zip(names, parts[4:8]):
+                if p.lower() == "active":
+                    reasons.add(n)
+        return {"sm_mhz": statistics.median(sm) if sm else None,
+                "sm_max_mhz": max(smax) if smax else None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def _dist_env():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return ws, rank, local
+
+
+def _cores() -> int:
+    try:
+        return len(os.sched_getaffinity(0))
+    except Exception:
+        return os.cpu_count() or 1
+
+
+# ---------------------------------------------------------------------------
+def run_oracle_bfs_sample(ro, col, sources, budget_s: float):
+    """Time the CPU oracle's BFS on sources until the budget is spent."""
+    import oracle
+    oracle.build()
+    deg = np.diff(ro)
+    edges, secs, used = 0, 0.0, []
+    for s in sources:
+        t0 = time.perf_counter()
+        d = oracle.bfs(ro, col, int(s))
+        secs += time.perf_counter() - t0
+        edges += int(deg[d >= 0].sum())
+        used.append(int(s))
+        if secs >= budget_s:
+            break
+    return edges, secs, used
+
+
+def reference_arm(args):
+    """The CPU oracle as the reference arm, on this arm's workload."""
+    ws, rank, _ = _dist_env()
+    if rank != 0:
+        return 0
+    from paper_1504_04804_gb300 import inputs
+    cfg = RMAT_CONFIGS[args.workload]
+    t0 = time.time()
+    g = inputs.rmat_graph(cfg["scale"], cfg["edge_factor"], seed=cfg["seed"])
+    gen_s = time.time() - t0
+    srcs = inputs.pick_sources(g.row_offsets, N_SOURCES, SOURCE_SEED)
+    import oracle
+    oracle.build()
+    deg = np.diff(g.row_offsets)
+    for i in range(args.warmup):
+        oracle.bfs(g.row_offsets, g.col_indices, int(srcs[i % len(srcs)]))
+    edges, secs = 0, 0.0
+    for i in range(args.steps):
+        s = int(srcs[i % len(srcs)])
+        t = time.perf_counter()
+        d = oracle.bfs(g.row_offsets, g.col_indices, s)
+        secs += time.perf_counter() - t
+        edges += int(deg[d >= 0].sum())
+    gteps = edges / secs / 1e9
+    line = {
+        "impl": "reference", "metric": METRIC, "value": gteps, "unit": "GTEPS",
+        "n_gpus": ws, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": secs / args.steps * 1e3, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "int32", "data": "synthetic",
+        "config": _config(args, g.nv, g.ne, "int32" if g.ne < 2**31 else "int64"),
+        "cpu_baseline": {"value": gteps, "unit": "GTEPS", "cores": 1, "kind": "oracle",
+                         "sample": f"one FIFO-queue BFS per step from the workload's seeded "
+                                   f"sources, single thread (graph generation {gen_s:.0f} s untimed)"},
+        "e2e": {"value": gteps, "unit": "GTEPS", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def _config(args, nv, ne, offsets):
+    cfg = RMAT_CONFIGS[args.workload]
+    return {"workload": f"R-MAT scale {cfg['scale']} ef {cfg['edge_factor']} "
+                        f"(a,b,c,d=0.57,0.19,0.19,0.05, seed {cfg['seed']}), direction-optimising BFS "
+                        f"from {N_SOURCES} seeded sources",
+            "nv": nv, "ne_directed": ne, "offsets": offsets, "sources_per_step": N_SOURCES,
+            "l2": "flushed before every traversal (256 MiB write, untimed)",
+            "alpha": args.alpha, "beta": args.beta}
+
+
+# ---------------------------------------------------------------------------
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="grx", choices=["grx", "reference"])
+    ap.add_argument("--workload", default="rmat22", choices=list(RMAT_CONFIGS))
+    ap.add_argument("--alpha", type=float, default=0.01)
+    ap.add_argument("--beta", type=float, default=0.1)
+    ap.add_argument("--cpu-budget", type=float, default=15.0,
+                    help="seconds of oracle BFS for the cpu_baseline sample")
+    ap.add_argument("--no-extra", action="store_true", help="skip SSSP/CC/PageRank timings")
+    args = ap.parse_args()
+    if args.impl == "reference":
+        return reference_arm(args)
+
+    import torch
+    ws, rank, local = _dist_env()
+    if ws > 1:
+        import torch.distributed as dist
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl")
+    from paper_1504_04804_gb300 import build, grx, inputs
+    build.build()
+    dev = torch.cuda.current_device()
+    stream = torch.cuda.current_stream()
+    cfg = RMAT_CONFIGS[args.workload]
+
+    ro, col, w = grx.rmat_graph_device(cfg["scale"], cfg["edge_factor"], seed=cfg["seed"],
+                                       wmax=cfg["wmax"], weight_seed=cfg["weight_seed"])
+    nv, ne = ro.numel() - 1, col.numel()
+    g = grx.graph_load_csr(ro, col, w, validate=False)
+    off_bytes = 8 if ne >= 2**31 else 4
+    ro_h = ro.cpu().numpy()
+    srcs = [int(s) for s in inputs.pick_sources(ro_h, N_SOURCES, SOURCE_SEED)]
+    deg_h = np.diff(ro_h)
+
+    # untimed instrumented pass: per-source byte model and TEPS numerator
+    st_opts = grx.opts(alpha=args.alpha, beta=args.beta, collect_stats=1)
+    per_src = {}
+    for s in srcs:
+        d = grx.bfs(g, s, opts=st_opts)
+        st = grx.last_stats(g)
+        reached = d.cpu().numpy() >= 0
+        per_src[s] = {"edges": int(deg_h[reached].sum()), "bytes": bfs_bytes(st, nv, off_bytes),
+                      "levels": st["levels"], "dirs": "".join("PL"[x] for x in st["dir"])}
+    grx.graph_status(g)
+
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device=f"cuda:{dev}")
+    o = grx.opts(alpha=args.alpha, beta=args.beta)
+    depth = torch.empty(nv, dtype=torch.int32, device=f"cuda:{dev}")
+    evs = [[torch.cuda.Event(enable_timing=True) for _ in range(4)]
+           for _ in range(args.steps * len(srcs))]
+    for ev in evs:              # torch creates the CUDA event on first record
+        for e in ev:
+            e.record(stream)
+
+    def traverse(s, ev=None):
+        if ev is not None:
+            o.ev_begin = ev[1].cuda_event
+            o.ev_end = ev[2].cuda_event
+            ev[0].record(stream)
+        else:
+            o.ev_begin = None
+            o.ev_end = None
+        grx.bfs(g, s, depth_out=depth, opts=o)
+        if ev is not None:
+            ev[3].record(stream)
+
+    for i in range(args.warmup):
+        for s in srcs:
+            flush.fill_(i & 0xff)
+            traverse(s)
+    torch.cuda.synchronize()
+    if ws > 1:
+        torch.distributed.barrier()
+    sampler = ClockSampler(dev)
+    time.sleep(0.3)
+    torch.cuda.synchronize()
+    t_wall0 = time.time()
+    k = 0
+    for step in range(args.steps):
+        for s in srcs:
+            flush.fill_(k & 0xff)
+            traverse(s, evs[k])
+            k += 1
+    torch.cuda.synchronize()
+    t_wall1 = time.time()
+    if ws > 1:
+        torch.distributed.barrier()
+    clocks = sampler.stop(t_wall0, t_wall1)
+    grx.graph_status(g)
+
+    step_ms = [e[0].elapsed_time(e[3]) for e in evs]        # whole bfs() call per traversal
+    kern_ms = [e[1].elapsed_time(e[2]) for e in evs]        # the traversal kernel alone
+    order = [s for _ in range(args.steps) for s in srcs]
+    edges_total = sum(per_src[s]["edges"] for s in order)
+    bytes_total = sum(per_src[s]["bytes"] for s in order)
+    t_total = sum(step_ms) / 1e3
+    t_max = t_total
+    if ws > 1:
+        t = torch.tensor([t_total], dtype=torch.float64, device=f"cuda:{dev}")
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        t_max = float(t.item())
+    gteps = edges_total * ws / t_max / 1e9
+    peak, peak_kind = _peaks()
+    achieved = bytes_total / (sum(kern_ms) / 1e3) / 1e9
+
+    # end to end through the public API with host buffers: the source goes in
+    # as a kernel argument, the depth array comes back to pinned host memory.
+    host_depth = torch.empty(nv, dtype=torch.int32, pin_memory=True)
+    e2e_t = 0.0
+    e2e_edges = 0
+    o.ev_begin = None
+    o.ev_end = None
+    torch.cuda.synchronize()
+    for step in range(max(1, args.steps // 2)):
+        for s in srcs:
+            flush.fill_(step & 0xff)
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            grx.bfs(g, s, depth_out=depth, opts=o)
+            host_depth.copy_(depth, non_blocking=True)
+            torch.cuda.current_stream().synchronize()
+            e2e_t += time.perf_counter() - t0
+            e2e_edges += per_src[s]["edges"]
+    e2e = {"value": e2e_edges / e2e_t / 1e9, "unit": "GTEPS", "h2d_bytes_per_step": 4 * len(srcs),
+           "d2h_bytes_per_step": 4 * nv * len(srcs)}
+
+    extra = {}
+    if not args.no_extra:
+        extra = other_primitives(grx, g, srcs, nv, ne, off_bytes, deg_h, flush, stream, peak)
+
+    cpu = None
+    if rank == 0:
+        col_h = col.cpu().numpy()
+        e_cpu, s_cpu, used = run_oracle_bfs_sample(ro_h, col_h, srcs, args.cpu_budget)
+        cpu = {"value": e_cpu / s_cpu / 1e9, "unit": "GTEPS", "cores": 1, "kind": "oracle",
+               "sample": f"FIFO-queue BFS from {len(used)} of the {len(srcs)} seeded sources on the "
+                         f"same graph, single thread, {s_cpu:.1f} s"}
+
+    if rank == 0:
+        line = {
+            "metric": METRIC, "value": gteps, "unit": "GTEPS", "n_gpus": ws,
+            "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": t_max / args.steps * 1e3, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "int32", "data": "synthetic",
+            "config": _config(args, nv, ne, "int32" if off_bytes == 4 else "int64"),
+            "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+                         "frac": achieved / peak, "traffic": None,
+                         "kernel": "k_bfs_persistent", "peak_kind": peak_kind,
+                         "bytes_per_launch": bytes_total / len(order),
+                         "launch_ms": sum(kern_ms) / len(kern_ms)},
+            "cpu_baseline": cpu,
+            "e2e": e2e,
+            "gpu_launches": 2 * len(order),
+            "clocks": clocks,
+            "detail": {"traversal_ms_median": statistics.median(step_ms),
+                       "kernel_ms_median": statistics.median(kern_ms),
+                       "levels": {str(s): per_src[s]["dirs"] for s in srcs[:4]}},
+            "extra": extra,
+        }
+        print(json.dumps(line), flush=True)
+    if ws > 1:
+        torch.distributed.destroy_process_group()
+    return 0
+
+
+def other_primitives(grx, g, srcs, nv, ne, off_bytes, deg_h, flush, stream, peak):
+    """SSSP, CC and PageRank on the same resident graph (CUDA events)."""
+    import torch
+    out = {}
+
+    def timed(fn, reps):
+        ts = []
+        for i in range(reps):
+            flush.fill_(i & 0xff)
+            a = torch.cuda.Event(enable_timing=True)
+            b = torch.cuda.Event(enable_timing=True)
+            a.record(stream)
+            fn(i)
+            b.record(stream)
+            torch.cuda.synchronize()
+            ts.append(a.elapsed_time(b))
+        return ts
+
+    # SSSP: 4 sources
+    so = grx.opts(collect_stats=1)
+    sbytes, sedges = [], []
+    for s in srcs[:4]:
+        d = grx.sssp(g, s, opts=so)
+        st = grx.last_stats(g)
+        sbytes.append(sssp_bytes(st, off_bytes))
+        sedges.append(int(deg_h[grx.as_uint32(d) != 0xFFFFFFFF].sum()))
+    ts = timed(lambda i: grx.sssp(g, srcs[i % 4]), 4)
+    grx.graph_status(g)
+    out["sssp"] = {"ms": ts, "gteps": sum(sedges) / (sum(ts) / 1e3) / 1e9,
+                   "roofline_frac": sum(sbytes) / (sum(ts) / 1e3) / 1e9 / peak}
+    # CC
+    lab = torch.empty(nv, dtype=torch.int32, device=flush.device)
+    ts = timed(lambda i: grx.cc(g, label_out=lab), 3)
+    grx.graph_status(g)
+    out["cc"] = {"ms": ts, "gteps": ne / (statistics.median(ts) / 1e3) / 1e9}
+    # PageRank 20 iterations
+    r = torch.empty(nv, dtype=torch.float32, device=flush.device)
+    ts = timed(lambda i: grx.pagerank(g, 0.85, 20, rank_out=r), 3)
+    pb = pr_bytes(nv, ne, off_bytes, 20)
+    out["pagerank"] = {"ms": ts, "iters": 20, "ms_per_iter": statistics.median(ts) / 20,
+                       "roofline_frac": pb / (statistics.median(ts) / 1e3) / 1e9 / peak}
+    return out
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -1,0 +1,187 @@
+/*
+ * grx.h -- C ABI of libgrx, a single-GPU (GB300, sm_103a) implementation of the
+ * frontier-traversal hot path of "Multi-GPU Graph Analytics" (Pan, Wang, Wu,
+ * Yang, Owens; arXiv 1504.04804): advance/filter over a CSR graph, the
+ * direction-optimising (push/pull) traversal of Sec. 6.1, and the BFS, SSSP,
+ * connected-components and PageRank primitives of Sec. 4 (Table 1,
+ * Algorithms 1-3), plus 64-source batched traversal.
+ *
+ * Conventions for every call:
+ *  - All calls are asynchronous on `stream` (a cudaStream_t passed as void*;
+ *    NULL = the legacy default stream).  Nothing synchronises the host unless
+ *    the call says so.  Device-side failures (a bounded wait that ran out, a
+ *    distance that overflowed) are recorded in the graph's status word and
+ *    returned by grx_graph_status().
+ *  - Output arrays are caller-owned DEVICE buffers of the documented size.
+ *    Input arrays are copied; the graph owns its copies.
+ *  - Errors are returned as grx_status codes; nothing throws across the ABI.
+ *    grx_last_error() gives a message for the calling thread's last failure.
+ *  - Vertex ids are int32 (nv < 2^31, else GRX_ERANGE).  The CSR must be
+ *    symmetric (every undirected edge stored in both rows, Sec. 7), without
+ *    self-loops or duplicate edges, rows sorted ascending.  The pull step,
+ *    CC and PageRank rely on symmetry; GRX_VALIDATE checks it on the device.
+ *  - One grx_ctx per host thread; a ctx and its graphs are not thread-safe.
+ *    Calls on the same graph must be issued on one stream (or ordered by the
+ *    caller), because a graph's traversal workspace is shared by its calls.
+ */
+#ifndef GRX_H
+#define GRX_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+    GRX_OK = 0,
+    GRX_EINVAL = -1,    /* bad argument or malformed graph */
+    GRX_ENOMEM = -2,    /* the allocator returned NULL */
+    GRX_ECUDA = -3,     /* a CUDA runtime call failed */
+    GRX_ETIMEOUT = -4,  /* a device-side bounded wait gave up */
+    GRX_ERANGE = -5,    /* a size or value exceeds the supported range */
+    GRX_EBUSY = -6      /* no free lane / slot */
+} grx_status;
+
+typedef struct grx_ctx grx_ctx;
+typedef struct grx_graph grx_graph;
+typedef struct grx_batch grx_batch;
+
+/* Device-memory allocator.  alloc must return a device pointer usable on
+ * `stream` (or NULL on failure); free receives the same pointer and size.
+ * The library keeps no pointer past the matching free. */
+typedef struct {
+    void *(*alloc)(size_t bytes, void *stream, void *user);
+    void (*free)(void *ptr, size_t bytes, void *stream, void *user);
+    void *user;
+} grx_allocator;
+
+/* Create a context bound to the current CUDA device.  allocator == NULL
+ * selects cudaMallocAsync/cudaFreeAsync.  The allocator struct is copied. */
+grx_status grx_ctx_create(const grx_allocator *allocator, grx_ctx **out);
+grx_status grx_ctx_destroy(grx_ctx *ctx);
+
+/* Message for the calling thread's most recent failed call ("" if none). */
+const char *grx_last_error(void);
+
+/* flags for graph_load_csr */
+#define GRX_HOST_PTRS   0x0   /* inputs are host pointers */
+#define GRX_DEVICE_PTRS 0x1   /* inputs are device pointers */
+#define GRX_VALIDATE    0x2   /* check offsets, column range, sortedness, no
+                                 self-loops, symmetry and weight symmetry on
+                                 the device (synchronises `stream`) */
+
+/* graph_load_csr -- Sec. 7 inputs: an undirected graph with self-loops and
+ * duplicate edges removed, stored as CSR (the paper's Csr, Appendix A).
+ *   nv, ne           vertex count (< 2^31) and directed edge count (< 2^32)
+ *   row_offsets      nv+1 entries, int32 (offsets_are_64bit = 0) or int64
+ *   col_indices      ne int32 vertex ids
+ *   weights          ne uint32 SSSP weights (Sec. 7), or NULL
+ *   flags            GRX_HOST_PTRS | GRX_DEVICE_PTRS, optionally GRX_VALIDATE
+ * The library copies the arrays into memory from the ctx allocator and owns
+ * them until graph_free.  Offsets are stored as int32 when ne < 2^31, else
+ * int64.  Returns GRX_EINVAL for malformed input (with GRX_VALIDATE), and
+ * GRX_ERANGE for nv >= 2^31 or ne >= 2^32. */
+grx_status graph_load_csr(grx_ctx *ctx, int64_t nv, int64_t ne,
+                          const void *row_offsets, int offsets_are_64bit,
+                          const int32_t *col_indices, const uint32_t *weights,
+                          int flags, void *stream, grx_graph **out);
+
+/* Free the graph's device memory (enqueued on the stream of the last call). */
+grx_status graph_free(grx_graph *g);
+
+/* Vertex and edge counts of a loaded graph. */
+grx_status grx_graph_info(const grx_graph *g, int64_t *nv, int64_t *ne);
+
+/* Synchronise `stream` and return (then clear) the device-side status word of
+ * the graph's traversals since the last call: GRX_OK, GRX_ETIMEOUT (a bounded
+ * wait ran out; outputs are not valid) or GRX_ERANGE (an SSSP distance did not
+ * fit below UINT32_MAX). */
+grx_status grx_graph_status(grx_graph *g, void *stream);
+
+/* ---- traversal options ------------------------------------------------- */
+#define GRX_DIR_AUTO 0   /* Sec. 6.1 push/pull switch with alpha (do_a), beta (do_b) */
+#define GRX_DIR_PUSH 1   /* top-down only (Algorithm 1) */
+#define GRX_DIR_PULL 2   /* bottom-up from the first level (for testing) */
+
+#define GRX_LOOP_PERSISTENT 0  /* one cooperative kernel runs every level */
+#define GRX_LOOP_HOST       1  /* one launch per level, host polls every 16 */
+#define GRX_LOOP_GRAPH      2  /* levels captured in a CUDA graph with a
+                                  device-evaluated WHILE condition node */
+
+typedef struct {
+    int direction;        /* GRX_DIR_* (BFS and multi-source BFS) */
+    float alpha;          /* push->pull when FV > BV * alpha (paper: do_a) */
+    float beta;           /* pull->push when FV < BV * beta  (paper: do_b) */
+    int loop;             /* GRX_LOOP_* */
+    int grid_blocks;      /* persistent grid size; 0 = SMs x occupancy */
+    int block_threads;    /* 0 = library default */
+    double timeout_s;     /* bound on every device-side wait; <= 0 = 5 s */
+    int collect_stats;    /* record per-level counters for grx_last_stats */
+    void *ev_begin;       /* optional cudaEvent_t recorded on `stream` just  */
+    void *ev_end;         /* before / after the traversal kernel(s) (timing) */
+} grx_opts;
+
+/* Library defaults: AUTO direction, alpha 0.01, beta 0.1 (Sec. 6.1's values
+ * for social graphs), persistent loop, full-occupancy grid, 5 s timeout. */
+void grx_opts_default(grx_opts *o);
+
+/* bfs -- Algorithm 1 (BFS) and, with direction AUTO, Algorithm 2 (DOBFS,
+ * Sec. 6.1).  depth_out: device int32[nv], hop distance from src, -1 if
+ * unreached.  parent_out: NULL or device int32[nv]; parent_out[src] = src,
+ * -1 if unreached, else a neighbour one level closer (any valid one).
+ * opts NULL = defaults.  Invalid src -> GRX_EINVAL. */
+grx_status bfs(grx_graph *g, int32_t src, int32_t *depth_out, int32_t *parent_out,
+               const grx_opts *opts, void *stream);
+
+/* sssp -- Table 1 SSSP: frontier label-correcting relaxation with atomicMin
+ * (the paper's min combiner, Sec. 3) until no distance improves.
+ * dist_out: device uint32[nv], UINT32_MAX if unreached.  Needs weights
+ * (else GRX_EINVAL).  A distance >= UINT32_MAX sets GRX_ERANGE status. */
+grx_status sssp(grx_graph *g, int32_t src, uint32_t *dist_out,
+                const grx_opts *opts, void *stream);
+
+/* cc -- Table 1 CC (Soman et al.'s hooking + pointer jumping).  label_out:
+ * device int32[nv], the minimum vertex id of the vertex's component. */
+grx_status cc(grx_graph *g, int32_t *label_out, void *stream);
+
+/* pagerank -- Algorithm 3 in the normalised mode with dangling compensation
+ * (Sec. 7): r0 = 1/N, then `iters` updates
+ *   r'[v] = (1-d)/N + d * (sum_{u in N(v)} r[u]/deg(u) + D/N),
+ *   D = sum of r over zero-degree vertices.
+ * rank_out: device float[nv].  FP32 arithmetic. */
+grx_status pagerank(grx_graph *g, float damping, int iters, float *rank_out, void *stream);
+
+/* ---- per-traversal counters (instrumented runs, collect_stats = 1) ------ */
+#define GRX_MAX_LEVELS_STATS 4096
+typedef struct {
+    int32_t levels;            /* levels run (frontier non-empty) */
+    int32_t dir[GRX_MAX_LEVELS_STATS];          /* 0 push, 1 pull */
+    int64_t frontier[GRX_MAX_LEVELS_STATS];     /* |Q| entering the level */
+    int64_t edges_examined[GRX_MAX_LEVELS_STATS];
+    int64_t vertices_scanned[GRX_MAX_LEVELS_STATS]; /* pull: |U| scanned */
+    int64_t discovered[GRX_MAX_LEVELS_STATS];   /* vertices labelled */
+} grx_trav_stats;
+
+/* Synchronise `stream` and copy the counters of the graph's last traversal
+ * that ran with collect_stats = 1. */
+grx_status grx_last_stats(grx_graph *g, void *stream, grx_trav_stats *out);
+
+/* ---- seeded input generation (device twins of the host generators) ------ */
+/* R-MAT edges (Sec. 7): edge i draws SplitMix64 values i*scale + l of stream
+ * `seed` for bit levels l; a draw's top 53 bits r pick quadrant A if r < t0,
+ * B if r < t1, C if r < t2, else D.  u_out, v_out: device int32[m]. */
+grx_status grx_rmat_edges(int scale, int64_t m, uint64_t seed, uint64_t t0, uint64_t t1,
+                          uint64_t t2, int32_t *u_out, int32_t *v_out, void *stream);
+
+/* Symmetric weights: w[e] = 1 + draw(seed, min(u,v)*nv + max(u,v)) mod wmax
+ * for CSR edge e = (u, v).  row_offsets int64 device [nv+1]. */
+grx_status grx_edge_weights(int64_t nv, int64_t ne, const int64_t *row_offsets,
+                            const int32_t *col_indices, uint32_t wmax, uint64_t seed,
+                            uint32_t *w_out, void *stream);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* GRX_H */

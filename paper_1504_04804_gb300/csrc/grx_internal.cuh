@@ -1,0 +1,288 @@
+// Internal declarations shared by the libgrx translation units.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+#include <stddef.h>
+
+#include "grx.h"
+
+#define GRX_FULL_MASK 0xffffffffu
+
+// ---------------------------------------------------------------------------
+// Host-side objects
+// ---------------------------------------------------------------------------
+struct grx_ctx {
+    grx_allocator alloc;
+    int has_alloc;
+    int device;
+    int num_sms;
+};
+
+// Device control block of a graph's traversals.  Barrier words live on their
+// own 128-byte lines so spinning blocks do not contend with counter updates.
+struct alignas(128) TravCtl {
+    // frontier ring: packed (count << 32 | edges) per slot; slot = level & 3
+    unsigned long long qpack[4];
+    unsigned int ucount[4];          // unvisited-list lengths, same ring
+    unsigned int disc[4];            // vertices discovered per level, same ring
+    int status;                      // first device-side error (0 = ok)
+    int levels_run;                  // levels completed by the last traversal
+    unsigned int pad0[18];
+    unsigned int bar_count;          // grid barrier arrivals
+    unsigned int pad1[31];
+    unsigned int bar_gen;            // grid barrier generation
+    unsigned int pad2[31];
+    // host-stepped mode: per-launch state, double buffered
+    long long hstate[2][8];
+    // PageRank dangling-mass accumulators (ring of 3)
+    double pr_dangling[3];
+    unsigned int flags;              // misc device flags (e.g. CC "changed")
+    unsigned int cc_changed[4];
+};
+
+struct DevStats {                    // device mirror of grx_trav_stats
+    int32_t levels;
+    int32_t dir[GRX_MAX_LEVELS_STATS];
+    unsigned long long frontier[GRX_MAX_LEVELS_STATS];
+    unsigned long long edges_examined[GRX_MAX_LEVELS_STATS];
+    unsigned long long vertices_scanned[GRX_MAX_LEVELS_STATS];
+    unsigned long long discovered[GRX_MAX_LEVELS_STATS];
+};
+
+struct grx_graph {
+    grx_ctx *ctx;
+    int32_t nv;
+    int64_t ne;
+    int off64;                       // row offsets stored as int64
+    void *ro;                        // int32 or int64 [nv+1]
+    int32_t *col;                    // [ne]
+    uint32_t *w;                     // [ne] or NULL
+    uint32_t *nz_bits;               // non-isolated vertex bitmap [words]
+    int64_t words;                   // (nv + 31) / 32 rounded up to 32
+    // non-isolated vertices in increasing id order and their row starts:
+    // active[i] = v, aoff[i] = ro[v], aoff[n_active] = ne.  With isolated
+    // rows dropped, edge e of this list is CSR edge e.
+    int32_t *active;
+    uint32_t *aoff;
+    int64_t n_active;
+    void *last_stream;
+    // ---- traversal workspace (allocated on first use) ----
+    int ws_ready;
+    uint32_t *visited;               // [words]
+    uint32_t *fbits[3];              // frontier bitmaps [words] each
+    int32_t *qv[3];                  // frontier vertices [nv] each
+    uint32_t *qe[3];                 // exclusive edge prefix per frontier slot
+    int32_t *ulist[2];               // unvisited lists [nv] each
+    TravCtl *ctl;
+    DevStats *stats;
+    // SSSP
+    int32_t *stamp;                  // [nv] round in which v was last queued
+    // PageRank
+    float *pr_c[2];                  // contribution r/deg ping-pong
+    float *pr_s;                     // cross-tile partial sums
+    int32_t *pr_fix;                 // per-tile row needing a fix-up
+    int64_t pr_fix_len;
+    // multi-source
+    unsigned long long *ms_cur, *ms_next, *ms_seen;   // [nv] each
+    int ms_ready;
+    // bookkeeping for frees
+    struct Alloc { void *p; size_t n; } allocs[48];
+    int nallocs;
+};
+
+// Allocation through the context allocator (or cudaMallocAsync).
+void *grx_alloc(grx_graph *g, size_t bytes, cudaStream_t s);
+void *grx_ctx_alloc(grx_ctx *c, size_t bytes, cudaStream_t s);
+void grx_ctx_free(grx_ctx *c, void *p, size_t bytes, cudaStream_t s);
+grx_status grx_ensure_workspace(grx_graph *g, cudaStream_t s);
+grx_status grx_ensure_ms_workspace(grx_graph *g, cudaStream_t s);
+
+// Error helpers (thread-local message).
+grx_status grx_fail(grx_status st, const char *fmt, ...);
+grx_status grx_cuda_fail(cudaError_t e, const char *what);
+#define GRX_CUDA(call)                                                         \
+    do {                                                                       \
+        cudaError_t _e = (call);                                               \
+        if (_e != cudaSuccess) return grx_cuda_fail(_e, #call);                \
+    } while (0)
+
+// Builds g->active / g->aoff / g->n_active (synchronises s once).
+grx_status grx_build_active(grx_graph *g, cudaStream_t s);
+
+// Options resolution.
+void grx_resolve_opts(const grx_opts *in, grx_opts *out);
+unsigned long long grx_timeout_ns(const grx_opts *o);
+
+// Kernel launchers (one per translation unit).
+grx_status grx_bfs_launch(grx_graph *g, int32_t src, int32_t *depth, int32_t *parent,
+                          const grx_opts *o, cudaStream_t s);
+grx_status grx_sssp_launch(grx_graph *g, int32_t src, uint32_t *dist, const grx_opts *o,
+                           cudaStream_t s);
+grx_status grx_cc_launch(grx_graph *g, int32_t *label, const grx_opts *o, cudaStream_t s);
+grx_status grx_pr_launch(grx_graph *g, float damping, int iters, float *rank,
+                         cudaStream_t s);
+
+// ---------------------------------------------------------------------------
+// Device helpers
+// ---------------------------------------------------------------------------
+#ifdef __CUDACC__
+
+__device__ __forceinline__ unsigned long long grx_globaltimer() {
+    unsigned long long t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
+}
+
+__device__ __forceinline__ unsigned int ld_acquire_u32(const unsigned int *p) {
+    unsigned int v;
+    asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+    return v;
+}
+
+__device__ __forceinline__ void st_release_u32(unsigned int *p, unsigned int v) {
+    asm volatile("st.release.gpu.global.u32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
+}
+
+__device__ __forceinline__ unsigned long long ld_relaxed_u64(const unsigned long long *p) {
+    unsigned long long v;
+    asm volatile("ld.relaxed.gpu.global.u64 %0, [%1];" : "=l"(v) : "l"(p) : "memory");
+    return v;
+}
+
+__device__ __forceinline__ unsigned int ld_relaxed_u32(const unsigned int *p) {
+    unsigned int v;
+    asm volatile("ld.relaxed.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+    return v;
+}
+
+// Record the first device-side error; later ones are dropped.
+__device__ __forceinline__ void grx_set_status(TravCtl *ctl, int st) {
+    atomicCAS(&ctl->status, 0, st);
+}
+
+// Grid-wide barrier for cooperative launches.  Every wait is bounded by
+// `timeout_ns` of global time: a block that gives up records GRX_ETIMEOUT and
+// returns false, and the caller leaves its loop.  Memory written before the
+// barrier by any block is visible after it (release by the last arriver,
+// acquire by the waiters).
+__device__ __forceinline__ bool grid_barrier(TravCtl *ctl, unsigned long long timeout_ns) {
+    __shared__ int s_ok;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        int ok = 1;
+        unsigned int gen = ld_acquire_u32(&ctl->bar_gen);
+        __threadfence();
+        unsigned int arrived = atomicAdd(&ctl->bar_count, 1u);
+        if (arrived == gridDim.x - 1) {
+            atomicExch(&ctl->bar_count, 0u);
+            __threadfence();
+            st_release_u32(&ctl->bar_gen, gen + 1);
+        } else {
+            unsigned long long t0 = grx_globaltimer();
+            while (ld_acquire_u32(&ctl->bar_gen) == gen) {
+                if (grx_globaltimer() - t0 > timeout_ns) {
+                    grx_set_status(ctl, GRX_ETIMEOUT);
+                    ok = 0;
+                    break;
+                }
+                __nanosleep(64);
+            }
+        }
+        __threadfence();
+        s_ok = ok;
+    }
+    __syncthreads();
+    return s_ok != 0;
+}
+
+__device__ __forceinline__ unsigned int lane_id() { return threadIdx.x & 31; }
+
+__device__ __forceinline__ unsigned int lanemask_lt() {
+    unsigned int m;
+    asm("mov.u32 %0, %%lanemask_lt;" : "=r"(m));
+    return m;
+}
+
+// Warp-aggregated append of (v, deg) to a frontier whose counter packs
+// (count << 32 | edge total).  One atomic per warp; positions and edge
+// prefixes come from the same atomic, so the prefix array stays monotone in
+// position order.  Must be called by all 32 lanes.
+__device__ __forceinline__ void warp_append_frontier(bool flag, int32_t v, uint32_t deg,
+                                                     int32_t *qv, uint32_t *qe,
+                                                     unsigned long long *ctr) {
+    unsigned int mask = __ballot_sync(GRX_FULL_MASK, flag);
+    if (mask == 0) return;
+    unsigned int lane = lane_id();
+    uint32_t x = flag ? deg : 0u;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        uint32_t y = __shfl_up_sync(GRX_FULL_MASK, x, o);
+        if (lane >= (unsigned)o) x += y;
+    }
+    uint32_t total = __shfl_sync(GRX_FULL_MASK, x, 31);
+    unsigned long long base = 0;
+    if (lane == 0)
+        base = atomicAdd(ctr, ((unsigned long long)__popc(mask) << 32) | (unsigned long long)total);
+    base = __shfl_sync(GRX_FULL_MASK, base, 0);
+    if (flag) {
+        uint32_t pos = (uint32_t)(base >> 32) + __popc(mask & lanemask_lt());
+        qv[pos] = v;
+        qe[pos] = (uint32_t)base + (x - deg);
+    }
+}
+
+// Warp-aggregated append of v to a plain list with a 32-bit counter.
+__device__ __forceinline__ void warp_append_list(bool flag, int32_t v, int32_t *list,
+                                                 unsigned int *ctr) {
+    unsigned int mask = __ballot_sync(GRX_FULL_MASK, flag);
+    if (mask == 0) return;
+    unsigned int base = 0;
+    if (lane_id() == 0) base = atomicAdd(ctr, (unsigned)__popc(mask));
+    base = __shfl_sync(GRX_FULL_MASK, base, 0);
+    if (flag) list[base + __popc(mask & lanemask_lt())] = v;
+}
+
+// Largest i in [0, n) with a[i] <= key (a ascending, a[0] <= key).
+template <typename T, typename K>
+__device__ __forceinline__ int64_t upper_index(const T *a, int64_t n, K key) {
+    int64_t lo = 0, hi = n;             // invariant: a[lo] <= key, answer in [lo, hi)
+    while (hi - lo > 1) {
+        int64_t mid = (lo + hi) >> 1;
+        if ((K)a[mid] <= key) lo = mid; else hi = mid;
+    }
+    return lo;
+}
+
+template <typename T>
+__device__ __forceinline__ T pick3(T a, T b, T c, int i) { return i == 0 ? a : (i == 1 ? b : c); }
+
+// Largest i in [0, n) with a[i] <= key, reading through L2 (a was written by
+// other blocks earlier in the same kernel).  Requires a[0] <= key.
+__device__ __forceinline__ int64_t upper_index_cg(const uint32_t *a, int64_t n, uint32_t key) {
+    int64_t lo = 0, hi = n;
+    while (hi - lo > 1) {
+        int64_t mid = (lo + hi) >> 1;
+        if (__ldcg(a + mid) <= key) lo = mid; else hi = mid;
+    }
+    return lo;
+}
+
+// Same search in shared memory.
+__device__ __forceinline__ int upper_index_smem(const uint32_t *a, int n, uint32_t key) {
+    int lo = 0, hi = n;
+    while (hi - lo > 1) {
+        int mid = (lo + hi) >> 1;
+        if (a[mid] <= key) lo = mid; else hi = mid;
+    }
+    return lo;
+}
+
+template <typename T>
+__device__ __forceinline__ T warp_sum(T x) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) x += __shfl_xor_sync(GRX_FULL_MASK, x, o);
+    return x;
+}
+
+#endif  // __CUDACC__

@@ -1,0 +1,70 @@
+"""Host-side checks of the C ABI: the library builds, loads and exports every
+entry point include/grx.h declares, and the binding declares each of them.
+No compute calls (no GPU here)."""
+import ctypes
+import os
+import re
+
+import pytest
+
+from paper_1504_04804_gb300 import build, grx
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+HEADERS = [os.path.join(ROOT, "include", f) for f in os.listdir(os.path.join(ROOT, "include"))
+           if f.endswith(".h")]
+
+
+def _declared_functions():
+    names = []
+    for h in HEADERS:
+        text = open(h).read()
+        text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+        for m in re.finditer(r"^[A-Za-z_][\w \*]*?\b([A-Za-z_]\w*)\s*\(", text, flags=re.M):
+            name = m.group(1)
+            if name not in ("if", "while", "for", "return", "sizeof", "defined"):
+                names.append(name)
+    return sorted(set(names))
+
+
+@pytest.fixture(scope="module")
+def libgrx():
+    build.build()
+    return ctypes.CDLL(grx.LIB_PATH)
+
+
+def test_header_declares_the_boundary():
+    names = _declared_functions()
+    for required in ("graph_load_csr", "graph_free", "bfs", "sssp", "cc", "pagerank"):
+        assert required in names
+
+
+def test_library_exports_every_declared_symbol(libgrx):
+    for name in _declared_functions():
+        assert hasattr(libgrx, name), f"libgrx.so does not export {name}"
+
+
+def test_binding_covers_every_declared_symbol():
+    bound = {name for name, _, _ in grx.SIGNATURES}
+    assert set(_declared_functions()) == bound
+
+
+def test_opts_struct_layout_matches_defaults(libgrx):
+    o = grx.grx_opts()
+    libgrx.grx_opts_default(ctypes.byref(o))
+    assert o.direction == grx.GRX_DIR_AUTO
+    assert abs(o.alpha - 0.01) < 1e-7 and abs(o.beta - 0.1) < 1e-7
+    assert o.loop == grx.GRX_LOOP_PERSISTENT and o.timeout_s == 5.0
+
+
+def test_argument_errors_without_gpu():
+    """Calls that fail argument checks return an error code before touching
+    the device."""
+    lib = grx.lib()
+    assert lib.bfs(None, 0, None, None, None, None) == grx.GRX_EINVAL
+    assert b"NULL graph" in lib.grx_last_error()
+    assert lib.sssp(None, 0, None, None, None) == grx.GRX_EINVAL
+    assert lib.cc(None, None, None) == grx.GRX_EINVAL
+    assert lib.pagerank(None, 0.85, 20, None, None) == grx.GRX_EINVAL
+    out = ctypes.c_void_p()
+    assert lib.graph_load_csr(None, 4, 0, None, 0, None, None, 0, None, ctypes.byref(out)) == grx.GRX_EINVAL
+    assert lib.grx_rmat_edges(0, 10, 1, 0, 0, 0, None, None, None) == grx.GRX_EINVAL

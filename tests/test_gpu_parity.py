@@ -1,0 +1,245 @@
+"""GPU parity: every libgrx entry point against the CPU oracle on the same
+seeded inputs.  BFS depths, SSSP distances and CC labels must match
+bit-for-bit; FP32 PageRank within a max relative error of 1e-5 per vertex
+against the FP64 oracle.  Parents (several valid answers) are checked by the
+oracle's invariant checker."""
+import itertools
+
+import numpy as np
+import pytest
+
+torch = pytest.importorskip("torch")
+
+import oracle
+from paper_1504_04804_gb300 import build, inputs
+
+pytestmark = pytest.mark.gpu
+
+PR_TOL = 1e-5
+MODES = {"auto": 0, "push": 1, "pull": 2}
+
+
+@pytest.fixture(scope="module")
+def grx():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    build.build()
+    from paper_1504_04804_gb300 import grx as g
+    return g
+
+
+def _graphs():
+    gs = {
+        "rmat10": inputs.rmat_graph(10, 16, seed=10, wmax=64, weight_seed=110),
+        "rmat13": inputs.rmat_graph(13, 16, seed=13, wmax=64, weight_seed=113),
+        "rmat14_ef4": inputs.rmat_graph(14, 4, seed=7, wmax=1000, weight_seed=3),
+        "grid64": inputs.grid_graph(64, 48, p_del=0.1, seed=64, wmax=1000, weight_seed=9),
+        "path": inputs.csr_from_edges(3000, [(i, i + 1) for i in range(2999)]),
+        "star": inputs.csr_from_edges(5001, [(0, i) for i in range(1, 5001)]),
+        "disconnected": inputs.csr_from_edges(
+            40, [(1, 2), (2, 3), (3, 1), (5, 6), (10, 11), (11, 12), (12, 13), (30, 31)]),
+    }
+    for name in ("path", "star", "disconnected"):
+        g = gs[name]
+        rows = np.repeat(np.arange(g.nv), np.diff(g.row_offsets))
+        lo = np.minimum(rows, g.col_indices).astype(np.uint64)
+        hi = np.maximum(rows, g.col_indices).astype(np.uint64)
+        g.weights = (1 + inputs.draw(5, lo * np.uint64(g.nv) + hi) % np.uint64(50)).astype(np.uint32)
+    return gs
+
+
+GRAPHS = _graphs()
+
+
+def _sources(g, n, seed=1):
+    n = min(n, int(np.count_nonzero(np.diff(g.row_offsets))))
+    return [int(s) for s in inputs.pick_sources(g.row_offsets, n, seed)]
+
+
+@pytest.fixture(scope="module")
+def loaded(grx):
+    return {name: grx.load(g, validate=True) for name, g in GRAPHS.items()}
+
+
+@pytest.mark.parametrize("name", list(GRAPHS))
+@pytest.mark.parametrize("mode", list(MODES))
+def test_bfs_matches_oracle(grx, loaded, name, mode):
+    g, dg = GRAPHS[name], loaded[name]
+    o = grx.opts(direction=MODES[mode])
+    for s in _sources(g, 4) + [g.nv - 1]:
+        d, p = grx.bfs(dg, s, opts=o, parent=True)
+        grx.graph_status(dg)
+        want = oracle.bfs(g.row_offsets, g.col_indices, s)
+        got = d.cpu().numpy()
+        assert np.array_equal(got, want), (name, mode, s, np.flatnonzero(got != want)[:10])
+        assert oracle.check_bfs(g.row_offsets, g.col_indices, s, got, p.cpu().numpy()) == 0
+
+
+@pytest.mark.parametrize("alpha,beta", [(0.01, 0.1), (1e-4, 1e-3), (0.5, 0.05), (1e-6, 10.0)])
+def test_dobfs_independent_of_switch_parameters(grx, loaded, alpha, beta):
+    g, dg = GRAPHS["rmat13"], loaded["rmat13"]
+    o = grx.opts(alpha=alpha, beta=beta, collect_stats=1)
+    for s in _sources(g, 3, seed=4):
+        d = grx.bfs(dg, s, opts=o)
+        st = grx.last_stats(dg)
+        assert np.array_equal(d.cpu().numpy(), oracle.bfs(g.row_offsets, g.col_indices, s))
+        assert st["levels"] >= 1 and st["frontier"][0] == 1
+
+
+def test_dobfs_switches_direction(grx, loaded):
+    g, dg = GRAPHS["rmat13"], loaded["rmat13"]
+    o = grx.opts(collect_stats=1)
+    s = _sources(g, 1)[0]
+    grx.bfs(dg, s, opts=o)
+    st = grx.last_stats(dg)
+    assert 1 in st["dir"], st["dir"]
+    want = oracle.bfs(g.row_offsets, g.col_indices, s)
+    assert st["levels"] == want.max() + 1
+    # newly discovered per level equals the oracle's level sizes
+    sizes = np.bincount(want[want >= 0])
+    assert st["discovered"][: len(sizes) - 1] == list(sizes[1:])
+
+
+def test_bfs_host_stepped_loop(grx, loaded):
+    for name in ("rmat10", "path", "grid64"):
+        g, dg = GRAPHS[name], loaded[name]
+        o = grx.opts(loop=grx.GRX_LOOP_HOST)
+        s = _sources(g, 1, seed=2)[0]
+        d = grx.bfs(dg, s, opts=o)
+        assert np.array_equal(d.cpu().numpy(), oracle.bfs(g.row_offsets, g.col_indices, s))
+
+
+def test_bfs_small_grids(grx, loaded):
+    g, dg = GRAPHS["rmat13"], loaded["rmat13"]
+    for blocks in (1, 2, 7, 152):
+        o = grx.opts(grid_blocks=blocks)
+        s = _sources(g, 1, seed=blocks)[0]
+        d = grx.bfs(dg, s, opts=o)
+        assert np.array_equal(d.cpu().numpy(), oracle.bfs(g.row_offsets, g.col_indices, s))
+
+
+@pytest.mark.parametrize("name", list(GRAPHS))
+def test_sssp_matches_oracle(grx, loaded, name):
+    g, dg = GRAPHS[name], loaded[name]
+    for s in _sources(g, 3) + [g.nv - 1]:
+        d = grx.sssp(dg, s)
+        grx.graph_status(dg)
+        got = grx.as_uint32(d)
+        want = oracle.sssp(g.row_offsets, g.col_indices, g.weights, s)
+        assert np.array_equal(got, want), (name, s)
+
+
+@pytest.mark.parametrize("name", list(GRAPHS))
+def test_cc_matches_oracle(grx, loaded, name):
+    g, dg = GRAPHS[name], loaded[name]
+    lab = grx.cc(dg)
+    grx.graph_status(dg)
+    assert np.array_equal(lab.cpu().numpy(), oracle.cc(g.row_offsets, g.col_indices))
+
+
+@pytest.mark.parametrize("name", list(GRAPHS))
+def test_pagerank_matches_oracle(grx, loaded, name):
+    g, dg = GRAPHS[name], loaded[name]
+    for iters in (0, 1, 20):
+        r = grx.pagerank(dg, 0.85, iters).cpu().numpy().astype(np.float64)
+        want = oracle.pagerank(g.row_offsets, g.col_indices, 0.85, iters)
+        rel = np.max(np.abs(r - want) / want)
+        assert rel <= PR_TOL, (name, iters, rel)
+        assert abs(r.sum() - 1.0) < 1e-4
+
+
+def test_exhaustive_6_vertex_graphs_as_one_union(grx):
+    """All 2^15 labelled graphs on 6 vertices as one disjoint union: CC over
+    the union, BFS/SSSP from a vertex of a seeded sample of the graphs."""
+    pairs = list(itertools.combinations(range(6), 2))
+    edges = []
+    for gi in range(1 << 15):
+        base = 6 * gi
+        edges += [(base + a, base + b) for i, (a, b) in enumerate(pairs) if gi >> i & 1]
+    u = inputs.csr_from_edges(6 << 15, edges)
+    rows = np.repeat(np.arange(u.nv), np.diff(u.row_offsets))
+    lo = np.minimum(rows, u.col_indices).astype(np.uint64)
+    hi = np.maximum(rows, u.col_indices).astype(np.uint64)
+    u.weights = (1 + inputs.draw(66, lo * np.uint64(u.nv) + hi) % np.uint64(3)).astype(np.uint32)
+    du = grx.load(u, validate=True)
+    assert np.array_equal(grx.cc(du).cpu().numpy(), oracle.cc(u.row_offsets, u.col_indices))
+    rng = np.random.default_rng(6)
+    for gi in rng.choice(1 << 15, size=64, replace=False):
+        s = int(6 * gi + rng.integers(0, 6))
+        for mode in (0, 1, 2):
+            d = grx.bfs(du, s, opts=grx.opts(direction=mode)).cpu().numpy()
+            assert np.array_equal(d, oracle.bfs(u.row_offsets, u.col_indices, s))
+        dist = grx.as_uint32(grx.sssp(du, s))
+        assert np.array_equal(dist, oracle.sssp(u.row_offsets, u.col_indices, u.weights, s))
+
+
+def test_graph_without_edges_and_isolated_source(grx):
+    g = inputs.csr_from_edges(100, [])
+    g.weights = np.zeros(0, dtype=np.uint32)
+    dg = grx.load(g)
+    d = grx.bfs(dg, 7).cpu().numpy()
+    assert d[7] == 0 and np.all(np.delete(d, 7) == -1)
+    dist = grx.as_uint32(grx.sssp(dg, 7))
+    assert dist[7] == 0 and np.all(np.delete(dist, 7) == 0xFFFFFFFF)
+    assert np.array_equal(grx.cc(dg).cpu().numpy(), np.arange(100))
+    r = grx.pagerank(dg, 0.85, 20).cpu().numpy()
+    assert np.allclose(r, 0.01, rtol=1e-6)
+    # isolated source in a graph with edges
+    g2 = GRAPHS["disconnected"]
+    d2 = grx.bfs(grx.load(g2), 0).cpu().numpy()
+    assert d2[0] == 0 and np.all(d2[1:] == -1)
+
+
+def test_invalid_arguments_raise(grx, loaded):
+    dg = loaded["rmat10"]
+    with pytest.raises(grx.GrxError):
+        grx.bfs(dg, -1)
+    with pytest.raises(grx.GrxError):
+        grx.bfs(dg, dg.nv)
+    with pytest.raises(grx.GrxError):
+        grx.sssp(grx.load(inputs.csr_from_edges(4, [(0, 1)])), 0)     # no weights
+    bad = inputs.csr_from_edges(4, [(0, 1), (1, 2)])
+    col = bad.col_indices.copy()
+    col[0] = 3                                                          # breaks symmetry
+    with pytest.raises(grx.GrxError):
+        grx.graph_load_csr(bad.row_offsets, col, validate=True)
+
+
+def test_device_generators_match_host(grx):
+    for scale, ef, seed in ((10, 16, 1), (14, 16, 14), (12, 3, 99)):
+        u, v = inputs.rmat_edges(scale, ef, seed)
+        du, dv = grx.rmat_edges(scale, ef, seed)
+        assert np.array_equal(du.cpu().numpy(), u) and np.array_equal(dv.cpu().numpy(), v)
+    g = inputs.rmat_graph(12, 16, seed=12, wmax=64, weight_seed=77)
+    ro, col, w = grx.rmat_graph_device(12, 16, seed=12, wmax=64, weight_seed=77)
+    assert np.array_equal(ro.cpu().numpy(), g.row_offsets)
+    assert np.array_equal(col.cpu().numpy(), g.col_indices)
+    assert np.array_equal(grx.as_uint32(w), g.weights)
+
+
+def test_load_from_device_arrays_int64_offsets(grx):
+    g = GRAPHS["rmat13"]
+    ro = torch.from_numpy(g.row_offsets).cuda()
+    col = torch.from_numpy(g.col_indices).cuda()
+    w = torch.from_numpy(g.weights.view(np.int32)).cuda()
+    dg = grx.graph_load_csr(ro, col, w, validate=True)
+    s = _sources(g, 1, seed=9)[0]
+    assert np.array_equal(grx.bfs(dg, s).cpu().numpy(), oracle.bfs(g.row_offsets, g.col_indices, s))
+    dg32 = grx.graph_load_csr(g.row_offsets.astype(np.int32), g.col_indices, g.weights)
+    assert np.array_equal(grx.as_uint32(grx.sssp(dg32, s)),
+                          oracle.sssp(g.row_offsets, g.col_indices, g.weights, s))
+
+
+def test_timeout_status_is_reported_and_context_survives(grx, loaded):
+    """A bounded wait that runs out sets GRX_ETIMEOUT on the host side and
+    leaves the context usable (no fault, no hang: the wait limit is tiny)."""
+    g, dg = GRAPHS["path"], loaded["path"]
+    o = grx.opts(timeout_s=1e-9, direction=grx.GRX_DIR_PUSH)
+    grx.bfs(dg, 0, opts=o)
+    try:
+        grx.graph_status(dg)
+    except grx.GrxError as e:
+        assert e.status == grx.GRX_ETIMEOUT
+    d = grx.bfs(dg, 0)
+    grx.graph_status(dg)
+    assert np.array_equal(d.cpu().numpy(), oracle.bfs(g.row_offsets, g.col_indices, 0))
