@@ -153,6 +153,34 @@ grx_status cc(grx_graph *g, int32_t *label_out, void *stream);
  * rank_out: device float[nv].  FP32 arithmetic. */
 grx_status pagerank(grx_graph *g, float damping, int iters, float *rank_out, void *stream);
 
+/* ---- allocation-free BFS ---------------------------------------------------
+ * bfs_noalloc -- the same traversal as bfs(), for callers that cannot allocate
+ * device memory (a host framework that owns the GPU's memory pool and forbids
+ * outside allocations, a latency-critical loop where cudaMalloc/cudaFree would
+ * synchronise the device, a request path that must not fail with
+ * out-of-memory).  The paper has no counterpart: this is a deployment variant.
+ *
+ * It allocates nothing.  The caller passes device arrays it owns:
+ *   row_offsets  int32[nv+1], col_indices int32[ne]: a symmetric CSR as for
+ *                graph_load_csr (not copied; must stay valid until the work
+ *                on `stream` completes)
+ *   depth_out    int32[nv] (as bfs), parent_out int32[nv] or NULL (as bfs)
+ *   status_out   int32[1] or NULL: receives the device-side status of this
+ *                call (0, or GRX_ETIMEOUT if a bounded wait ran out)
+ * All traversal scratch lives in one fixed __device__ array sized for
+ * GRX_NOALLOC_MAX_NV vertices (about 17 MB), which every GPU that loads the
+ * library holds until the process exits.  nv above that limit returns
+ * GRX_ERANGE; ne must be below 2^31.  opts as for bfs (collect_stats must be 0).
+ * The first call on a device looks up the array's device address (once per
+ * device, with that device current); make that first call before any CUDA
+ * stream capture.  Every call shares the array and clears what it needs;
+ * calls whose GPU work overlaps race on it, so order them (one stream). */
+#define GRX_NOALLOC_MAX_NV (1 << 19)
+grx_status bfs_noalloc(int64_t nv, int64_t ne, const int32_t *row_offsets,
+                       const int32_t *col_indices, int32_t src, int32_t *depth_out,
+                       int32_t *parent_out, int32_t *status_out, const grx_opts *opts,
+                       void *stream);
+
 /* ---- per-traversal counters (instrumented runs, collect_stats = 1) ------ */
 #define GRX_MAX_LEVELS_STATS 4096
 typedef struct {

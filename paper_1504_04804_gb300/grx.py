@@ -75,6 +75,7 @@ SIGNATURES = [
     ("cc", _I, [_P, _P, _P]),
     ("pagerank", _I, [_P, ctypes.c_float, _I, _P, _P]),
     ("grx_last_stats", _I, [_P, _P, _P]),
+    ("bfs_noalloc", _I, [_I64, _I64, _P, _P, ctypes.c_int32, _P, _P, _P, _P, _P]),
     ("grx_rmat_edges", _I, [_I, _I64, _U64, _U64, _U64, _U64, _P, _P, _P]),
     ("grx_edge_weights", _I, [_I64, _I64, _P, _P, ctypes.c_uint32, _U64, _P, _P]),
 ]
@@ -287,6 +288,28 @@ def pagerank(g: Graph, damping: float = 0.85, iters: int = 20, rank_out=None, st
     _check(lib().pagerank(g.handle, float(damping), int(iters), r.data_ptr(), _stream_ptr(stream)),
            "pagerank")
     return r
+
+
+GRX_NOALLOC_MAX_NV = 1 << 19
+
+
+def bfs_noalloc(row_offsets: torch.Tensor, col_indices: torch.Tensor, src: int, depth_out=None,
+                parent_out=None, status_out=None, opts: grx_opts | None = None, stream=None):
+    """BFS over caller-owned device CSR arrays (int32 offsets) without any
+    device allocation by the library: for callers that cannot allocate.  The
+    output tensors, if not given, are created here by torch (the library
+    itself allocates nothing).  Limited to GRX_NOALLOC_MAX_NV vertices; calls
+    share one fixed scratch array, so calls overlapping on the GPU race."""
+    nv = row_offsets.numel() - 1
+    dev = row_offsets.device.index
+    d = _out(depth_out, nv, torch.int32, dev)
+    _check(lib().bfs_noalloc(nv, col_indices.numel(), row_offsets.data_ptr(),
+                             col_indices.data_ptr() if col_indices.numel() else None, int(src),
+                             d.data_ptr(), parent_out.data_ptr() if parent_out is not None else None,
+                             status_out.data_ptr() if status_out is not None else None,
+                             ctypes.byref(opts) if opts is not None else None, _stream_ptr(stream)),
+           "bfs_noalloc")
+    return d
 
 
 def graph_status(g: Graph, stream=None):
