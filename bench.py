@@ -31,6 +31,9 @@ sys.path.insert(0, ROOT)
 METRIC = "BFS GTEPS & HBM-roofline % at R-MAT 22/26; batched-query p50/p99 latency"
 RMAT_CONFIGS = {
     "rmat16": dict(scale=16, edge_factor=16, seed=16, wmax=64, weight_seed=116),
+    "rmat18": dict(scale=18, edge_factor=16, seed=18, wmax=64, weight_seed=118),
+    "rmat20": dict(scale=20, edge_factor=16, seed=20, wmax=64, weight_seed=120),
+    "rmat21": dict(scale=21, edge_factor=16, seed=21, wmax=64, weight_seed=121),
     "rmat22": dict(scale=22, edge_factor=16, seed=22, wmax=64, weight_seed=122),
     "rmat26": dict(scale=26, edge_factor=16, seed=26, wmax=64, weight_seed=126),
 }
@@ -90,7 +93,7 @@ class ClockSampler:
               "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
               "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
 
-    def __init__(self, gpu_index: int, period_ms: int = 50):
+    def __init__(self, gpu_index: int, period_ms: int = 20):
         self.proc = None
         self.lines = []
         try:

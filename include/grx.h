@@ -119,6 +119,9 @@ typedef struct {
     int block_threads;    /* 0 = library default */
     double timeout_s;     /* bound on every device-side wait; <= 0 = 5 s */
     int collect_stats;    /* record per-level counters for grx_last_stats */
+    int exact_fv;         /* 1: FV is the frontier's exact edge count (known
+                             for free from the append counter) instead of
+                             the paper's |Q|*E/V estimate */
     void *ev_begin;       /* optional cudaEvent_t recorded on `stream` just  */
     void *ev_end;         /* before / after the traversal kernel(s) (timing) */
 } grx_opts;
@@ -190,6 +193,7 @@ typedef struct {
     int64_t edges_examined[GRX_MAX_LEVELS_STATS];
     int64_t vertices_scanned[GRX_MAX_LEVELS_STATS]; /* pull: |U| scanned */
     int64_t discovered[GRX_MAX_LEVELS_STATS];   /* vertices labelled */
+    int64_t level_ns[GRX_MAX_LEVELS_STATS];     /* device time of the level */
 } grx_trav_stats;
 
 /* Synchronise `stream` and copy the counters of the graph's last traversal

@@ -1,33 +1,57 @@
 // BFS and direction-optimising BFS (Algorithms 1 and 2, Sec. 6.1).
 //
 // Design (one GPU, GB300):
-//  * The whole traversal is one cooperative persistent kernel; levels are
-//    separated by a bounded grid barrier, so no host round trip or launch
-//    happens per level (the per-iteration overhead l of Sec. 5.2).  A
+//  * The whole traversal, including the initialisation of the outputs and
+//    bitmaps, is one cooperative persistent kernel.  Levels are separated by a
+//    flag-based grid barrier with bounded waits, so no host round trip or
+//    launch happens per level (the per-iteration overhead l of Sec. 5.2).  A
 //    host-stepped variant (one launch per level) exists for comparison.
-//  * Push (top-down) advance+filter are fused (Sec. 6.3): each frontier slot
-//    carries the exclusive prefix of its vertices' degrees, produced by the
-//    same warp-aggregated atomic that appends the vertex, so the next level
-//    splits the frontier's edges into equal tiles with no separate scan.  A
-//    tile's threads find their source vertex by binary search in shared
-//    memory; the visited bitmap is the filter (test, then atomicOr).
-//  * Pull (bottom-up): one thread per unvisited vertex scans its neighbours
-//    in order and stops at the first one in the frontier bitmap (edge
-//    skipping); no atomics on labels.  The unvisited list is split into the
-//    newly discovered vertices (appended to the next push-ready frontier,
-//    so pull->push costs nothing, Sec. 6.1) and the still-unvisited list.
+//  * Work inside a level is warp-independent: no block-wide barrier, so a
+//    warp waiting on memory never holds up its neighbours.
+//  * Push (top-down): advance and filter are fused (Sec. 6.3).  A frontier
+//    slot holds the vertex, its row start and the exclusive prefix of the
+//    frontier's degrees; all three come from the append that discovered the
+//    vertex (one warp-aggregated atomic), so the next level cuts the
+//    frontier's edges into equal warp tiles with no scan pass and reads a
+//    tile's rows in one round trip.  Each warp owns a contiguous range of
+//    tiles; each lane takes a run of PUSH_ITEMS consecutive edges and keeps
+//    their loads, bitmap probes and atomics in flight together.  The visited
+//    bitmap is the filter (test, then atomicOr; lanes of a warp that aim at
+//    the same vertex send one atomic; the winner labels the vertex).
+//  * Pull (bottom-up, Sec. 6.1): each lane takes PULL_PER_LANE unvisited
+//    vertices and probes their first PULL_LIGHT neighbours against the
+//    frontier bitmap at once; the vertices with longer lists and no hit yet
+//    are scanned by groups of PULL_GROUP lanes, PULL_GROUP neighbours per step,
+//    stopping at the first hit (edge skipping).  No atomics on labels.  The
+//    unvisited set is split into newly discovered vertices (appended, with
+//    degree and row start, to the next frontier, so pull->push costs nothing)
+//    and the still-unvisited list.
 //  * Direction switch (Sec. 6.1): FV = |Q|*E/V, BV = |U|*V/|P|; push->pull
-//    once when FV > BV*alpha, pull->push when FV < BV*beta.  Every block
-//    evaluates it identically from the device counters after the barrier.
+//    once when FV > BV*alpha, pull->push when FV < BV*beta.  With
+//    exact_fv = 1, FV is the frontier's exact edge count, which the append
+//    atomic already provides.  Every block evaluates the rule identically.
 #include <cstdio>
+#include <cstring>
 
 #include "grx_internal.cuh"
 
 namespace {
 
+#ifndef GRX_PUSH_ITEMS
+#define GRX_PUSH_ITEMS 8
+#endif
+#ifndef GRX_PUSH_DEDUP
+#define GRX_PUSH_DEDUP 1
+#endif
+
 constexpr int BFS_BLOCK = 256;
-constexpr int PUSH_ITEMS = 8;
-constexpr int PUSH_TILE = BFS_BLOCK * PUSH_ITEMS;   // edges per tile
+constexpr int WARPS = BFS_BLOCK / 32;
+constexpr int PUSH_ITEMS = GRX_PUSH_ITEMS;
+constexpr int WTILE = 32 * PUSH_ITEMS;              // edges per warp tile
+constexpr int PULL_LIGHT = 2;                       // neighbours probed per vertex first
+constexpr int PULL_PER_LANE = 4;
+constexpr int PULL_WCH = 32 * PULL_PER_LANE;        // candidates per warp chunk
+constexpr int PULL_GROUP = 8;                       // lanes per long list
 
 enum { DIR_PUSH = 0, DIR_PULL = 1 };
 
@@ -36,7 +60,7 @@ struct LevelState {
     int dir;
     int switched;     // push->pull has happened
     int back;         // pull->push has happened (final)
-    int first_pull;   // pull level without an unvisited list yet: scan all vertices
+    int first_pull;   // pull level without an unvisited list yet: scan the bitmaps
     int fwrite;       // this level sets F_{L+1} bits for discovered vertices
     int fprev;        // F_L holds the frontier's bits
     int fclear;       // this level clears F_{L-1} (word by word from Q_{L-1})
@@ -51,6 +75,7 @@ template <typename OffT>
 struct BfsArgs {
     int32_t nv;
     int64_t ne;
+    int64_t words;
     const OffT *ro;
     const int32_t *col;
     const uint32_t *nz;
@@ -58,24 +83,39 @@ struct BfsArgs {
     uint32_t *F[3];
     int32_t *Q[3];
     uint32_t *E[3];
+    OffT *R[3];
     int32_t *U[2];
     int32_t *depth;
     int32_t *parent;
     TravCtl *ctl;
+    unsigned int *bar_flags;
     DevStats *stats;
     int mode;
+    int exact_fv;
     float alpha, beta;
     unsigned long long timeout_ns;
     int32_t src;
 };
 
 template <typename OffT>
-struct PushSmem {
-    uint32_t qe[PUSH_TILE + 1];
-    int32_t u[PUSH_TILE + 1];
-    OffT rs[PUSH_TILE + 1];
-    int64_t i0;
-    int n;
+struct PushWarpSmem {
+    uint32_t qe[WTILE + 2];
+    int32_t u[WTILE + 1];
+    OffT rs[WTILE + 1];
+};
+
+template <typename OffT>
+struct PullWarpSmem {
+    int32_t slot[PULL_WCH];
+    OffT hb[PULL_WCH];
+    OffT he[PULL_WCH];
+    int32_t hpar[PULL_WCH];
+};
+
+template <typename OffT>
+union WarpSmem {
+    PushWarpSmem<OffT> p;
+    PullWarpSmem<OffT> l;
 };
 
 template <typename OffT>
@@ -90,7 +130,7 @@ __device__ LevelState initial_state(const BfsArgs<OffT> &a) {
     s.fprev = a.mode != GRX_DIR_PUSH;
     s.fclear = 0;
     s.done = 0;
-    uint32_t deg = (uint32_t)(a.ro[a.src + 1] - a.ro[a.src]);
+    uint32_t deg = (uint32_t)(__ldg(a.ro + a.src + 1) - __ldg(a.ro + a.src));
     s.q = deg > 0 ? 1u : 0u;
     s.T = deg;
     s.qprev = 0;
@@ -126,9 +166,9 @@ __device__ LevelState next_state(const BfsArgs<OffT> &a, const LevelState &st, b
         ns.dir = DIR_PULL;
         ns.fwrite = 1;
     } else {
-        // Sec. 6.1 estimates: FV = |Q|*E/V, BV = |U|*V/|P|, P = visited incl. Q
+        // Sec. 6.1: FV = |Q|*E/V (or the exact frontier edge count), BV = |U|*V/|P|
         double V = (double)a.nv, E = (double)a.ne;
-        double FV = (double)ns.q * E / V;
+        double FV = a.exact_fv ? (double)ns.T : (double)ns.q * E / V;
         double BV = (double)(a.nv - (long long)ns.vcount) * V / (double)ns.vcount;
         if (st.dir == DIR_PUSH && !st.switched && FV > BV * (double)a.alpha) {
             ns.dir = DIR_PULL;
@@ -144,152 +184,308 @@ __device__ LevelState next_state(const BfsArgs<OffT> &a, const LevelState &st, b
 }
 
 template <typename OffT, bool PARENT, bool STATS>
-__device__ void push_level(const BfsArgs<OffT> &a, const LevelState &st, PushSmem<OffT> &sm) {
+__device__ void push_level(const BfsArgs<OffT> &a, const LevelState &st, PushWarpSmem<OffT> &w) {
     const int L = st.L;
+    const unsigned int lane = threadIdx.x & 31;
     const int32_t *Qv = pick3(a.Q[0], a.Q[1], a.Q[2], L % 3);
     const uint32_t *Qe = pick3(a.E[0], a.E[1], a.E[2], L % 3);
+    const OffT *Qr = pick3(a.R[0], a.R[1], a.R[2], L % 3);
     int32_t *Qv_out = pick3(a.Q[0], a.Q[1], a.Q[2], (L + 1) % 3);
     uint32_t *Qe_out = pick3(a.E[0], a.E[1], a.E[2], (L + 1) % 3);
+    OffT *Qr_out = pick3(a.R[0], a.R[1], a.R[2], (L + 1) % 3);
     uint32_t *Fout = pick3(a.F[0], a.F[1], a.F[2], (L + 1) % 3);
     unsigned long long *ctr = &a.ctl->qpack[(L + 1) & 3];
-    const uint32_t q = st.q;
+    const int64_t q = st.q;
     const uint64_t T = st.T;
-    const uint64_t ntiles = (T + PUSH_TILE - 1) / PUSH_TILE;
-    for (uint64_t tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
-        const uint64_t e0 = tile * PUSH_TILE;
-        const uint64_t e1 = min(T, e0 + PUSH_TILE);
-        if (threadIdx.x == 0) {
-            int64_t i0 = upper_index_cg(Qe, q, (uint32_t)e0);
-            int64_t i1 = upper_index_cg(Qe, q, (uint32_t)(e1 - 1));
-            int n = (int)(i1 - i0 + 1);
-            if (n > PUSH_TILE + 1) {      // only possible with a malformed graph
-                grx_set_status(a.ctl, GRX_EINVAL);
-                n = PUSH_TILE + 1;
+    const uint64_t ntiles = (T + WTILE - 1) / WTILE;
+    const uint64_t nwarps = (uint64_t)gridDim.x * WARPS;
+    const uint64_t gw = (uint64_t)blockIdx.x * WARPS + (threadIdx.x >> 5);
+    // each warp owns a contiguous range of tiles: one search for its first element
+    const uint64_t per = (ntiles + nwarps - 1) / nwarps;
+    const uint64_t tb0 = gw * per;
+    const uint64_t tb1 = min(ntiles, tb0 + per);
+    if (tb0 >= tb1) return;
+    int64_t i0 = warp_upper_index_cg(Qe, q, (uint32_t)(tb0 * WTILE));
+    for (uint64_t tile = tb0; tile < tb1; ++tile) {
+        const uint64_t e0 = tile * WTILE;
+        const uint32_t e1 = (uint32_t)min(T, e0 + WTILE);
+        // frontier elements starting before e1, 32 per round; w.qe[n] ends up
+        // holding the start of the first element past the tile
+        int n = 0;
+        for (;;) {
+            const int64_t idx = i0 + n + lane;
+            uint32_t qe = 0xffffffffu;
+            if (idx < q) qe = __ldcg(Qe + idx);
+            const bool in = idx < q && qe < e1;
+            if (n + (int)lane <= WTILE + 1) w.qe[n + lane] = qe;
+            if (in && n + (int)lane <= WTILE) {
+                w.u[n + lane] = __ldcg(Qv + idx);
+                w.rs[n + lane] = __ldcg(Qr + idx);
             }
-            sm.i0 = i0;
-            sm.n = n;
+            const int cnt = __popc(__ballot_sync(GRX_FULL_MASK, in));
+            n += cnt;
+            if (cnt < 32) break;
+            if (n > WTILE) {              // only possible with a malformed graph
+                if (lane == 0) grx_set_status(a.ctl, GRX_EINVAL);
+                n = WTILE;
+                break;
+            }
         }
-        __syncthreads();
-        const int64_t i0 = sm.i0;
-        const int n = sm.n;
-        for (int j = threadIdx.x; j < n; j += BFS_BLOCK) {
-            int32_t u = __ldcg(Qv + i0 + j);
-            sm.qe[j] = __ldcg(Qe + i0 + j);
-            sm.u[j] = u;
-            sm.rs[j] = __ldg(a.ro + u);
-        }
-        __syncthreads();
-#pragma unroll 2
+        __syncwarp();
+        const uint32_t next_start = w.qe[n];
+        // a run of PUSH_ITEMS consecutive edges per lane
+        const uint64_t t0 = e0 + (uint64_t)lane * PUSH_ITEMS;
+        int32_t v[PUSH_ITEMS];
+        int32_t par[PUSH_ITEMS];
+        uint32_t valid = 0;
+#pragma unroll
         for (int k = 0; k < PUSH_ITEMS; ++k) {
-            const uint64_t e = e0 + (uint64_t)(k * BFS_BLOCK + threadIdx.x);
-            bool disc = false;
-            int32_t v = 0;
-            uint32_t deg = 0;
-            if (e < e1) {
-                int j = upper_index_smem(sm.qe, n, (uint32_t)e);
-                int32_t u = sm.u[j];
-                v = __ldg(a.col + sm.rs[j] + (OffT)((uint32_t)e - sm.qe[j]));
-                const uint32_t bit = 1u << (v & 31);
-                uint32_t *wp = a.visited + (v >> 5);
-                if (!(__ldcg(wp) & bit)) {
-                    uint32_t old = atomicOr(wp, bit);
-                    if (!(old & bit)) {
-                        disc = true;
-                        a.depth[v] = L + 1;
-                        if (PARENT) a.parent[v] = u;
-                        deg = (uint32_t)(__ldg(a.ro + v + 1) - __ldg(a.ro + v));
-                        if (st.fwrite && deg) atomicOr(Fout + (v >> 5), bit);
-                    }
+            v[k] = 0;
+            par[k] = 0;
+        }
+        if (t0 < e1) {
+            int j = upper_index_smem(w.qe, n, (uint32_t)t0);
+#pragma unroll
+            for (int k = 0; k < PUSH_ITEMS; ++k) {
+                const uint32_t e = (uint32_t)t0 + k;
+                if (e < e1) {
+                    while (w.qe[j + 1] <= e) ++j;
+                    v[k] = __ldg(a.col + w.rs[j] + (OffT)(e - w.qe[j]));
+                    if (PARENT) par[k] = w.u[j];
+                    valid |= 1u << k;
                 }
             }
-            warp_append_frontier(disc && deg > 0, v, deg, Qv_out, Qe_out, ctr);
         }
-        __syncthreads();
-    }
-    if (STATS && blockIdx.x == 0 && threadIdx.x == 0 && L < GRX_MAX_LEVELS_STATS) {
-        a.stats->edges_examined[L] = T;
-        a.stats->vertices_scanned[L] = q;
+        uint32_t wv[PUSH_ITEMS];
+#pragma unroll
+        for (int k = 0; k < PUSH_ITEMS; ++k)
+            wv[k] = (valid >> k & 1u) ? __ldcg(a.visited + (v[k] >> 5)) : 0xffffffffu;
+        uint32_t cand = 0;
+#pragma unroll
+        for (int k = 0; k < PUSH_ITEMS; ++k) {
+            const bool c = !((wv[k] >> (v[k] & 31)) & 1u);
+#if GRX_PUSH_DEDUP
+            // lanes aiming at the same vertex: only the lowest one tries to claim it
+            const unsigned int same = __match_any_sync(GRX_FULL_MASK, c ? v[k] : -1 - (int)lane);
+            if (c && (same & lanemask_lt()) == 0) cand |= 1u << k;
+#else
+            if (c) cand |= 1u << k;
+#endif
+        }
+        uint32_t old[PUSH_ITEMS];
+#pragma unroll
+        for (int k = 0; k < PUSH_ITEMS; ++k)
+            old[k] = (cand >> k & 1u) ? atomicOr(a.visited + (v[k] >> 5), 1u << (v[k] & 31)) : 0xffffffffu;
+        uint32_t disc = 0;
+#pragma unroll
+        for (int k = 0; k < PUSH_ITEMS; ++k)
+            if (!((old[k] >> (v[k] & 31)) & 1u)) disc |= 1u << k;
+        uint32_t deg[PUSH_ITEMS];
+        OffT rb[PUSH_ITEMS], re[PUSH_ITEMS];
+#pragma unroll
+        for (int k = 0; k < PUSH_ITEMS; ++k) {
+            rb[k] = 0;
+            re[k] = 0;
+            if (disc >> k & 1u) {
+                rb[k] = __ldg(a.ro + v[k]);
+                re[k] = __ldg(a.ro + v[k] + 1);
+            }
+        }
+        uint32_t app = 0;
+#pragma unroll
+        for (int k = 0; k < PUSH_ITEMS; ++k) {
+            deg[k] = (uint32_t)(re[k] - rb[k]);
+            if (disc >> k & 1u) {
+                a.depth[v[k]] = L + 1;
+                if (PARENT) a.parent[v[k]] = par[k];
+                if (deg[k]) {
+                    app |= 1u << k;
+                    if (st.fwrite) atomicOr(Fout + (v[k] >> 5), 1u << (v[k] & 31));
+                }
+            }
+        }
+        warp_append_items<PUSH_ITEMS, OffT>(v, deg, rb, app, Qv_out, Qe_out, Qr_out, ctr);
+        // the element holding e1 starts the next tile
+        i0 = (next_start == e1) ? i0 + n : i0 + n - 1;
+        __syncwarp();
     }
 }
 
 template <typename OffT, bool PARENT, bool STATS>
-__device__ void pull_level(const BfsArgs<OffT> &a, const LevelState &st) {
+__device__ void pull_level(const BfsArgs<OffT> &a, const LevelState &st, PullWarpSmem<OffT> &w,
+                           unsigned long long &scanned_e, unsigned long long &scanned_v) {
     const int L = st.L;
+    const unsigned int lane = threadIdx.x & 31;
     const uint32_t *Fin = pick3(a.F[0], a.F[1], a.F[2], L % 3);
     uint32_t *Fout = pick3(a.F[0], a.F[1], a.F[2], (L + 1) % 3);
     int32_t *Qv_out = pick3(a.Q[0], a.Q[1], a.Q[2], (L + 1) % 3);
     uint32_t *Qe_out = pick3(a.E[0], a.E[1], a.E[2], (L + 1) % 3);
+    OffT *Qr_out = pick3(a.R[0], a.R[1], a.R[2], (L + 1) % 3);
     unsigned long long *ctr = &a.ctl->qpack[(L + 1) & 3];
     const int32_t *Uin = (L & 1) ? a.U[1] : a.U[0];
     int32_t *Uout = (L & 1) ? a.U[0] : a.U[1];
     unsigned int *uctr = &a.ctl->ucount[(L + 1) & 3];
     const bool first = st.first_pull != 0;
-    const int64_t count = first ? (int64_t)a.nv : (int64_t)st.ucount;
-    const int64_t span = (count + 31) & ~(int64_t)31;
-    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
-    unsigned long long scanned_e = 0, scanned_v = 0;
-    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < span; i += stride) {
-        int32_t v = -1;
-        if (i < count) {
-            if (first) {
-                uint32_t w = __ldg(a.nz + (i >> 5)) & ~__ldcg(a.visited + (i >> 5));
-                if ((w >> (i & 31)) & 1u) v = (int32_t)i;
-            } else {
-                v = __ldcg(Uin + i);
+    const int64_t nchunks = first ? (a.words + PULL_PER_LANE - 1) / PULL_PER_LANE
+                                  : ((int64_t)st.ucount + PULL_WCH - 1) / PULL_WCH;
+    const int64_t nwarps = (int64_t)gridDim.x * WARPS;
+    const int64_t gw = (int64_t)blockIdx.x * WARPS + (threadIdx.x >> 5);
+    for (int64_t c = gw; c < nchunks; c += nwarps) {
+        // 1. candidates: lane takes vertex k*32+lane of the chunk
+        int32_t v[PULL_PER_LANE];
+        if (first) {
+            uint32_t any = 0;
+#pragma unroll
+            for (int k = 0; k < PULL_PER_LANE; ++k) {
+                const int64_t wd = c * PULL_PER_LANE + k;
+                const uint32_t bits = wd < a.words ? (__ldg(a.nz + wd) & ~__ldcg(a.visited + wd)) : 0u;
+                any |= bits;
+                v[k] = ((bits >> lane) & 1u) ? (int32_t)(wd * 32 + lane) : -1;
+            }
+            if (any == 0) continue;                  // same words in every lane
+        } else {
+#pragma unroll
+            for (int k = 0; k < PULL_PER_LANE; ++k) {
+                const int64_t i = c * PULL_WCH + k * 32 + lane;
+                v[k] = i < (int64_t)st.ucount ? __ldcg(Uin + i) : -1;
             }
         }
-        bool found = false, still = false;
-        uint32_t deg = 0;
-        if (v >= 0) {
-            const OffT b = __ldg(a.ro + v), e = __ldg(a.ro + v + 1);
-            int32_t par = -1;
-            OffT k = b;
-            for (; k < e; ++k) {
-                int32_t u = __ldg(a.col + k);
-                if ((__ldcg(Fin + (u >> 5)) >> (u & 31)) & 1u) {
-                    par = u;
-                    break;
+        // 2. light phase: the first PULL_LIGHT neighbours of every candidate, all in flight
+        OffT b[PULL_PER_LANE], e[PULL_PER_LANE];
+#pragma unroll
+        for (int k = 0; k < PULL_PER_LANE; ++k) {
+            b[k] = 0;
+            e[k] = 0;
+            if (v[k] >= 0) {
+                b[k] = __ldg(a.ro + v[k]);
+                e[k] = __ldg(a.ro + v[k] + 1);
+            }
+        }
+        int32_t u0[PULL_PER_LANE], u1[PULL_PER_LANE];
+#pragma unroll
+        for (int k = 0; k < PULL_PER_LANE; ++k) {
+            u0[k] = b[k] < e[k] ? __ldg(a.col + b[k]) : -1;
+            u1[k] = b[k] + 1 < e[k] ? __ldg(a.col + b[k] + 1) : -1;
+        }
+        uint32_t f0[PULL_PER_LANE], f1[PULL_PER_LANE];
+#pragma unroll
+        for (int k = 0; k < PULL_PER_LANE; ++k) {
+            f0[k] = u0[k] >= 0 ? __ldcg(Fin + (u0[k] >> 5)) : 0u;
+            f1[k] = u1[k] >= 0 ? __ldcg(Fin + (u1[k] >> 5)) : 0u;
+        }
+        int32_t par[PULL_PER_LANE];
+        uint32_t heavy = 0;
+#pragma unroll
+        for (int k = 0; k < PULL_PER_LANE; ++k) {
+            par[k] = -1;
+            if (u0[k] >= 0 && ((f0[k] >> (u0[k] & 31)) & 1u)) par[k] = u0[k];
+            else if (u1[k] >= 0 && ((f1[k] >> (u1[k] & 31)) & 1u)) par[k] = u1[k];
+            if (STATS && v[k] >= 0) {
+                scanned_v += 1;
+                scanned_e += (unsigned long long)min((OffT)PULL_LIGHT, e[k] - b[k]);
+            }
+            if (v[k] >= 0 && par[k] < 0 && e[k] - b[k] > PULL_LIGHT) heavy |= 1u << k;
+        }
+        // 3. heavy phase: the warp's longer lists, PULL_GROUP lanes each
+        int nh = 0;
+        int hpos[PULL_PER_LANE];
+#pragma unroll
+        for (int k = 0; k < PULL_PER_LANE; ++k) {
+            const unsigned int m = __ballot_sync(GRX_FULL_MASK, heavy >> k & 1u);
+            hpos[k] = nh + __popc(m & lanemask_lt());
+            if (heavy >> k & 1u) {
+                w.hb[hpos[k]] = b[k] + PULL_LIGHT;
+                w.he[hpos[k]] = e[k];
+            }
+            nh += __popc(m);
+        }
+        __syncwarp();
+        const int grp = (int)(lane / PULL_GROUP), gl = (int)(lane % PULL_GROUP);
+        for (int h0 = 0; h0 < nh; h0 += 32 / PULL_GROUP) {
+            const int h = h0 + grp;
+            OffT hb = 0, he = 0;
+            if (h < nh) {
+                hb = w.hb[h];
+                he = w.he[h];
+            }
+            int32_t found = -1;
+            bool done = h >= nh;
+            while (__any_sync(GRX_FULL_MASK, !done)) {
+                int32_t uu = -1;
+                bool hit = false;
+                if (!done && hb + gl < he) {
+                    uu = __ldg(a.col + hb + gl);
+                    hit = (__ldcg(Fin + (uu >> 5)) >> (uu & 31)) & 1u;
+                }
+                const unsigned int gm = (__ballot_sync(GRX_FULL_MASK, hit) >> (grp * PULL_GROUP)) &
+                                        ((1u << PULL_GROUP) - 1u);
+                const int32_t first_hit =
+                    __shfl_sync(GRX_FULL_MASK, uu, grp * PULL_GROUP + (gm ? __ffs(gm) - 1 : 0));
+                if (!done) {
+                    if (STATS && gl == 0)
+                        scanned_e += (unsigned long long)(gm ? __ffs(gm) : min((OffT)PULL_GROUP, he - hb));
+                    if (gm) {
+                        found = first_hit;
+                        done = true;
+                    } else {
+                        hb += PULL_GROUP;
+                        done = hb >= he;
+                    }
                 }
             }
-            if (STATS) {
-                scanned_v += 1;
-                scanned_e += (unsigned long long)((k < e ? k + 1 : e) - b);
+            if (h < nh && gl == 0) w.hpar[h] = found;
+        }
+        __syncwarp();
+        // 4. label the found vertices; append found / still-unvisited
+        uint32_t fmask = 0, smask = 0;
+        uint32_t deg[PULL_PER_LANE];
+#pragma unroll
+        for (int k = 0; k < PULL_PER_LANE; ++k) {
+            if (heavy >> k & 1u) par[k] = w.hpar[hpos[k]];
+            deg[k] = (uint32_t)(e[k] - b[k]);
+            const bool fnd = v[k] >= 0 && par[k] >= 0;
+            if (fnd) {
+                a.depth[v[k]] = L + 1;
+                if (PARENT) a.parent[v[k]] = par[k];
+                fmask |= 1u << k;
+            } else if (v[k] >= 0) {
+                smask |= 1u << k;
             }
-            if (par >= 0) {
-                found = true;
-                a.depth[v] = L + 1;
-                if (PARENT) a.parent[v] = par;
-                const uint32_t bit = 1u << (v & 31);
-                atomicOr(a.visited + (v >> 5), bit);
-                deg = (uint32_t)(e - b);
-                if (st.fwrite) atomicOr(Fout + (v >> 5), bit);
-            } else {
-                still = true;
+            if (first) {
+                // slot k of every lane lies in the same bitmap word: one atomic per word
+                const uint32_t bits = __reduce_or_sync(GRX_FULL_MASK, fnd ? 1u << lane : 0u);
+                if (lane == 0 && bits) {
+                    const int64_t wd = c * PULL_PER_LANE + k;
+                    atomicOr(a.visited + wd, bits);
+                    if (st.fwrite) atomicOr(Fout + wd, bits);
+                }
+            } else if (fnd) {
+                const uint32_t bit = 1u << (v[k] & 31);
+                atomicOr(a.visited + (v[k] >> 5), bit);
+                if (st.fwrite) atomicOr(Fout + (v[k] >> 5), bit);
             }
         }
-        warp_append_frontier(found, v, deg, Qv_out, Qe_out, ctr);
-        warp_append_list(still, v, Uout, uctr);
-    }
-    if (STATS) {
-        scanned_e = warp_sum(scanned_e);
-        scanned_v = warp_sum(scanned_v);
-        if (lane_id() == 0 && L < GRX_MAX_LEVELS_STATS) {
-            if (scanned_e) atomicAdd(&a.stats->edges_examined[L], scanned_e);
-            if (scanned_v) atomicAdd(&a.stats->vertices_scanned[L], scanned_v);
-        }
+        warp_append_items<PULL_PER_LANE, OffT>(v, deg, b, fmask, Qv_out, Qe_out, Qr_out, ctr);
+        warp_append_list_items<PULL_PER_LANE>(v, smask, Uout, uctr);
+        __syncwarp();
     }
 }
 
 template <typename OffT, bool PARENT, bool STATS>
-__device__ void run_level(const BfsArgs<OffT> &a, const LevelState &st, PushSmem<OffT> &sm) {
+__device__ void run_level(const BfsArgs<OffT> &a, const LevelState &st, WarpSmem<OffT> &w) {
     const int L = st.L;
     if (blockIdx.x == 0 && threadIdx.x == 0) {
         a.ctl->qpack[(L + 2) & 3] = 0ull;
         a.ctl->ucount[(L + 2) & 3] = 0u;
         if (STATS && L < GRX_MAX_LEVELS_STATS) {
+            a.stats->level_t0[L] = grx_globaltimer();
             a.stats->dir[L] = st.dir;
             a.stats->frontier[L] = st.q;
             a.stats->levels = L + 1;
+            if (st.dir == DIR_PUSH) {
+                a.stats->edges_examined[L] = st.T;
+                a.stats->vertices_scanned[L] = st.q;
+            }
         }
     }
     if (st.fclear) {
@@ -300,45 +496,103 @@ __device__ void run_level(const BfsArgs<OffT> &a, const LevelState &st, PushSmem
              i += (int64_t)gridDim.x * blockDim.x)
             Fp[__ldcg(Qp + i) >> 5] = 0u;
     }
-    if (st.dir == DIR_PUSH) push_level<OffT, PARENT, STATS>(a, st, sm);
-    else pull_level<OffT, PARENT, STATS>(a, st);
+    if (st.dir == DIR_PUSH) {
+        push_level<OffT, PARENT, STATS>(a, st, w.p);
+    } else {
+        unsigned long long scanned_e = 0, scanned_v = 0;
+        pull_level<OffT, PARENT, STATS>(a, st, w.l, scanned_e, scanned_v);
+        if (STATS) {
+            scanned_e = warp_sum(scanned_e);
+            scanned_v = warp_sum(scanned_v);
+            if ((threadIdx.x & 31) == 0 && L < GRX_MAX_LEVELS_STATS) {
+                if (scanned_e) atomicAdd(&a.stats->edges_examined[L], scanned_e);
+                if (scanned_v) atomicAdd(&a.stats->vertices_scanned[L], scanned_v);
+            }
+        }
+    }
+}
+
+// Phase 0 of a traversal: depth = -1 (0 at src), parent = -1 (src at src),
+// visited = {src}, frontier bitmaps = {src} / empty, the frontier counters
+// and the first frontier slot.  Every word is written by exactly one thread,
+// so clearing and seeding need no barrier between them.
+template <typename OffT, bool PARENT>
+__device__ void init_phase(const BfsArgs<OffT> &a, const LevelState &st0) {
+    const int64_t tid = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    const int32_t src = a.src;
+    for (int64_t v = tid; v < a.nv; v += stride) {
+        a.depth[v] = v == src ? 0 : -1;
+        if (PARENT) a.parent[v] = v == src ? src : -1;
+    }
+    const int64_t sw = src >> 5;
+    const uint32_t sb = 1u << (src & 31);
+    const bool use_f = a.mode != GRX_DIR_PUSH;
+    for (int64_t w = tid; w < a.words; w += stride) {
+        a.visited[w] = w == sw ? sb : 0u;
+        if (use_f) {
+            a.F[0][w] = (w == sw && st0.q) ? sb : 0u;
+            a.F[1][w] = 0u;
+            a.F[2][w] = 0u;
+        }
+    }
+    if (tid == 0) {
+        a.Q[0][0] = src;
+        a.E[0][0] = 0;
+        a.R[0][0] = __ldg(a.ro + src);
+        a.ctl->qpack[0] = st0.q ? ((1ull << 32) | st0.T) : 0ull;
+        for (int i = 1; i < 4; ++i) a.ctl->qpack[i] = 0ull;
+        for (int i = 0; i < 4; ++i) a.ctl->ucount[i] = 0u;
+    }
 }
 
 template <typename OffT, bool PARENT, bool STATS>
-__global__ void __launch_bounds__(BFS_BLOCK) k_bfs_persistent(BfsArgs<OffT> a) {
+__global__ void __launch_bounds__(BFS_BLOCK, 3) k_bfs_persistent(BfsArgs<OffT> a) {
     __shared__ LevelState s_st;
-    __shared__ PushSmem<OffT> sm;
+    __shared__ WarpSmem<OffT> wsm[WARPS];
+    WarpSmem<OffT> &w = wsm[threadIdx.x >> 5];
+    FlagBarrier bar{a.bar_flags, &a.ctl->bar_release, a.ctl, a.timeout_ns, 0u};
     if (threadIdx.x == 0) s_st = initial_state(a);
     __syncthreads();
+    init_phase<OffT, PARENT>(a, s_st);
+    if (!flag_barrier(bar)) return;
     for (;;) {
         const LevelState st = s_st;
         if (st.done) break;
-        run_level<OffT, PARENT, STATS>(a, st, sm);
-        if (!grid_barrier(a.ctl, a.timeout_ns)) break;
+        run_level<OffT, PARENT, STATS>(a, st, w);
+        if (!flag_barrier(bar)) return;
         if (threadIdx.x == 0) s_st = next_state(a, st, STATS);
         __syncthreads();
     }
-    if (blockIdx.x == 0 && threadIdx.x == 0) a.ctl->levels_run = s_st.L;
+    if (blockIdx.x == 0 && threadIdx.x == 0) {
+        a.ctl->levels_run = s_st.L;
+        if (STATS && s_st.L <= GRX_MAX_LEVELS_STATS) a.stats->level_t0[s_st.L] = grx_globaltimer();
+    }
 }
 
-// Host-stepped variant: launch i runs level i.  The state of level i is
-// derived at the start of launch i from the state launch i-1 stored and the
-// counters it left, so no block ever waits on another.
+// Host-stepped variant: launch 0 initialises, launch i >= 1 runs level i-1.
+// The state of a level is derived at the start of its launch from the state
+// the previous launch stored and the counters it left, so no block ever
+// waits on another.
 template <typename OffT, bool PARENT, bool STATS>
 __global__ void __launch_bounds__(BFS_BLOCK) k_bfs_step(BfsArgs<OffT> a, int launch) {
     __shared__ LevelState s_st;
-    __shared__ PushSmem<OffT> sm;
+    __shared__ WarpSmem<OffT> wsm[WARPS];
     static_assert(sizeof(LevelState) <= sizeof(long long) * 8, "state must fit hstate");
-    if (threadIdx.x == 0) {
-        LevelState st;
-        if (launch == 0) {
-            st = initial_state(a);
-        } else {
-            LevelState prev;
-            memcpy(&prev, (const void *)a.ctl->hstate[(launch - 1) & 1], sizeof prev);
-            st = prev.done ? prev : next_state(a, prev, STATS);
+    if (launch == 0) {
+        if (threadIdx.x == 0) s_st = initial_state(a);
+        __syncthreads();
+        init_phase<OffT, PARENT>(a, s_st);
+        if (blockIdx.x == 0 && threadIdx.x == 0) {
+            LevelState st = s_st;
+            memcpy((void *)a.ctl->hstate[0], &st, sizeof st);
         }
-        s_st = st;
+        return;
+    }
+    if (threadIdx.x == 0) {
+        LevelState prev;
+        memcpy(&prev, (const void *)a.ctl->hstate[(launch - 1) & 1], sizeof prev);
+        s_st = (launch == 1 || prev.done) ? prev : next_state(a, prev, STATS);
     }
     __syncthreads();
     const LevelState st = s_st;
@@ -347,27 +601,7 @@ __global__ void __launch_bounds__(BFS_BLOCK) k_bfs_step(BfsArgs<OffT> a, int lau
         if (st.done) a.ctl->levels_run = st.L;
     }
     if (st.done) return;
-    run_level<OffT, PARENT, STATS>(a, st, sm);
-}
-
-__global__ void k_bfs_init(int32_t src, const void *ro, int off64, int32_t *depth, int32_t *parent,
-                           uint32_t *visited, uint32_t *F0, int32_t *Q0, uint32_t *E0,
-                           TravCtl *ctl, DevStats *stats, int stats_on) {
-    int64_t b = off64 ? ((const int64_t *)ro)[src] : ((const int32_t *)ro)[src];
-    int64_t e = off64 ? ((const int64_t *)ro)[src + 1] : ((const int32_t *)ro)[src + 1];
-    uint32_t deg = (uint32_t)(e - b);
-    depth[src] = 0;
-    if (parent) parent[src] = src;
-    visited[src >> 5] = 1u << (src & 31);
-    if (F0 && deg) F0[src >> 5] = 1u << (src & 31);
-    Q0[0] = src;
-    E0[0] = 0;
-    ctl->qpack[0] = deg ? ((1ull << 32) | deg) : 0ull;
-    for (int i = 1; i < 4; ++i) ctl->qpack[i] = 0ull;
-    for (int i = 0; i < 4; ++i) ctl->ucount[i] = 0u;
-    ctl->bar_count = 0u;
-    ctl->levels_run = 0;
-    if (stats_on) stats->levels = 0;
+    run_level<OffT, PARENT, STATS>(a, st, wsm[threadIdx.x >> 5]);
 }
 
 template <typename OffT>
@@ -376,6 +610,7 @@ BfsArgs<OffT> make_args(grx_graph *g, int32_t src, int32_t *depth, int32_t *pare
     BfsArgs<OffT> a;
     a.nv = g->nv;
     a.ne = g->ne;
+    a.words = g->words;
     a.ro = (const OffT *)g->ro;
     a.col = g->col;
     a.nz = g->nz_bits;
@@ -384,14 +619,17 @@ BfsArgs<OffT> make_args(grx_graph *g, int32_t src, int32_t *depth, int32_t *pare
         a.F[i] = g->fbits[i];
         a.Q[i] = g->qv[i];
         a.E[i] = g->qe[i];
+        a.R[i] = (OffT *)g->qr[i];
     }
     a.U[0] = g->ulist[0];
     a.U[1] = g->ulist[1];
     a.depth = depth;
     a.parent = parent;
     a.ctl = g->ctl;
+    a.bar_flags = g->bar_flags;
     a.stats = g->stats;
     a.mode = o->direction;
+    a.exact_fv = o->exact_fv;
     a.alpha = o->alpha;
     a.beta = o->beta;
     a.timeout_ns = grx_timeout_ns(o);
@@ -408,7 +646,7 @@ grx_status launch_typed(grx_graph *g, int32_t src, int32_t *depth, int32_t *pare
         // Poll the done flag every 16 launches; a traversal has at most nv levels.
         long long st_host[8];
         if (o->ev_begin) GRX_CUDA(cudaEventRecord((cudaEvent_t)o->ev_begin, s));
-        for (int launch = 0; launch <= g->nv; ++launch) {
+        for (int launch = 0; launch <= g->nv + 1; ++launch) {
             k_bfs_step<OffT, PARENT, STATS><<<blocks, BFS_BLOCK, 0, s>>>(a, launch);
             if ((launch & 15) == 15) {
                 GRX_CUDA(cudaMemcpyAsync(st_host, (const void *)g->ctl->hstate[launch & 1],
@@ -431,7 +669,10 @@ grx_status launch_typed(grx_graph *g, int32_t src, int32_t *depth, int32_t *pare
             return grx_fail(GRX_ECUDA, "bfs: persistent kernel does not fit on an SM");
     }
     int max_grid = max_blocks_per_sm * g->ctx->num_sms;
+    if (max_grid > GRX_MAX_GRID) max_grid = GRX_MAX_GRID;
     int blocks = o->grid_blocks > 0 && o->grid_blocks < max_grid ? o->grid_blocks : max_grid;
+    GRX_CUDA(cudaMemsetAsync(g->bar_flags, 0, sizeof(unsigned int) * (size_t)blocks, s));
+    GRX_CUDA(cudaMemsetAsync(&g->ctl->bar_release, 0, sizeof(unsigned int), s));
     void *args[] = {(void *)&a};
     if (o->ev_begin) GRX_CUDA(cudaEventRecord((cudaEvent_t)o->ev_begin, s));
     GRX_CUDA(cudaLaunchCooperativeKernel((const void *)k_bfs_persistent<OffT, PARENT, STATS>,
@@ -456,19 +697,7 @@ grx_status launch_off(grx_graph *g, int32_t src, int32_t *depth, int32_t *parent
 
 grx_status grx_bfs_launch(grx_graph *g, int32_t src, int32_t *depth, int32_t *parent,
                           const grx_opts *o, cudaStream_t s) {
-    const size_t nv = (size_t)g->nv;
-    const size_t wb = (size_t)g->words * 4;
-    GRX_CUDA(cudaMemsetAsync(depth, 0xff, nv * 4, s));
-    if (parent) GRX_CUDA(cudaMemsetAsync(parent, 0xff, nv * 4, s));
-    GRX_CUDA(cudaMemsetAsync(g->visited, 0, wb, s));
-    const bool use_f = o->direction != GRX_DIR_PUSH;
-    if (use_f)
-        for (int i = 0; i < 3; ++i) GRX_CUDA(cudaMemsetAsync(g->fbits[i], 0, wb, s));
     if (o->collect_stats) GRX_CUDA(cudaMemsetAsync(g->stats, 0, sizeof(DevStats), s));
-    k_bfs_init<<<1, 1, 0, s>>>(src, g->ro, g->off64, depth, parent, g->visited,
-                               use_f ? g->fbits[0] : nullptr, g->qv[0], g->qe[0], g->ctl,
-                               g->stats, o->collect_stats);
-    GRX_CUDA(cudaGetLastError());
     return g->off64 ? launch_off<int64_t>(g, src, depth, parent, o, s)
                     : launch_off<int32_t>(g, src, depth, parent, o, s);
 }

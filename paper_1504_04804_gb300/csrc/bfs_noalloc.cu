@@ -28,11 +28,13 @@ constexpr int kMaxDevices = 64;
 
 struct NoallocScratch {
     TravCtl ctl;
+    unsigned int bar_flags[GRX_MAX_GRID];
     uint32_t visited[kWords];
     uint32_t fbits[3][kWords];
     uint32_t nz[kWords];
     int32_t qv[3][kMaxNv];
     uint32_t qe[3][kMaxNv];
+    int32_t qr[3][kMaxNv];
     int32_t ulist[2][kMaxNv];
 };
 
@@ -137,10 +139,12 @@ extern "C" grx_status bfs_noalloc(int64_t nv, int64_t ne, const int32_t *row_off
         g.fbits[i] = sc->fbits[i];
         g.qv[i] = sc->qv[i];
         g.qe[i] = sc->qe[i];
+        g.qr[i] = sc->qr[i];
     }
     g.ulist[0] = sc->ulist[0];
     g.ulist[1] = sc->ulist[1];
     g.ctl = &sc->ctl;
+    g.bar_flags = sc->bar_flags;
     g.ws_ready = 1;
     st = grx_bfs_launch(&g, src, depth_out, parent_out, &o, s);
     if (st != GRX_OK) return st;

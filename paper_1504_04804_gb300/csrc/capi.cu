@@ -314,13 +314,15 @@ grx_status grx_ensure_workspace(grx_graph *g, cudaStream_t s) {
         g->fbits[i] = (uint32_t *)grx_alloc(g, wb, s);
         g->qv[i] = (int32_t *)grx_alloc(g, nv * 4, s);
         g->qe[i] = (uint32_t *)grx_alloc(g, nv * 4, s);
+        g->qr[i] = grx_alloc(g, nv * (g->off64 ? 8 : 4), s);
     }
     for (int i = 0; i < 2; ++i) g->ulist[i] = (int32_t *)grx_alloc(g, nv * 4, s);
     g->ctl = (TravCtl *)grx_alloc(g, sizeof(TravCtl), s);
+    g->bar_flags = (unsigned int *)grx_alloc(g, sizeof(unsigned int) * GRX_MAX_GRID, s);
     g->stats = (DevStats *)grx_alloc(g, sizeof(DevStats), s);
     g->stamp = (int32_t *)grx_alloc(g, nv * 4, s);
-    bool ok = g->visited && g->ctl && g->stats && g->stamp;
-    for (int i = 0; i < 3; ++i) ok = ok && g->fbits[i] && g->qv[i] && g->qe[i];
+    bool ok = g->visited && g->ctl && g->bar_flags && g->stats && g->stamp;
+    for (int i = 0; i < 3; ++i) ok = ok && g->fbits[i] && g->qv[i] && g->qe[i] && g->qr[i];
     for (int i = 0; i < 2; ++i) ok = ok && g->ulist[i];
     if (!ok) return grx_fail(GRX_ENOMEM, "traversal workspace allocation failed (nv=%d)", g->nv);
     GRX_CUDA(cudaMemsetAsync(g->ctl, 0, sizeof(TravCtl), s));
@@ -377,6 +379,8 @@ extern "C" grx_status grx_last_stats(grx_graph *g, void *stream, grx_trav_stats 
         out->edges_examined[i] = in ? (int64_t)h->edges_examined[i] : 0;
         out->vertices_scanned[i] = in ? (int64_t)h->vertices_scanned[i] : 0;
         out->discovered[i] = in ? (int64_t)h->discovered[i] : 0;
+        out->level_ns[i] = in && h->level_t0[i + 1] >= h->level_t0[i]
+                               ? (int64_t)(h->level_t0[i + 1] - h->level_t0[i]) : 0;
     }
     free(h);
     return GRX_OK;

@@ -30,6 +30,7 @@ struct CcArgs {
     int64_t n_active;
     int32_t *label;
     TravCtl *ctl;
+    unsigned int *bar_flags;
     unsigned long long timeout_ns;
 };
 
@@ -103,15 +104,16 @@ __device__ void jump_phase(const CcArgs &a) {
 
 __global__ void __launch_bounds__(CC_BLOCK) k_cc_persistent(CcArgs a) {
     __shared__ CcSmem sm;
+    FlagBarrier bar{a.bar_flags, &a.ctl->bar_release, a.ctl, a.timeout_ns, 0u};
     for (int64_t v = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; v < a.nv;
          v += (int64_t)gridDim.x * blockDim.x)
         a.label[v] = (int32_t)v;
     if (blockIdx.x == 0 && threadIdx.x < 4) a.ctl->cc_changed[threadIdx.x] = 0u;
-    if (!grid_barrier(a.ctl, a.timeout_ns)) return;
+    if (!flag_barrier(bar)) return;
     for (int round = 0;; ++round) {
         if (blockIdx.x == 0 && threadIdx.x == 0) a.ctl->cc_changed[(round + 2) & 3] = 0u;
         hook_phase(a, round, sm);
-        if (!grid_barrier(a.ctl, a.timeout_ns)) return;
+        if (!flag_barrier(bar)) return;
         if (threadIdx.x == 0) sm.changed = ld_relaxed_u32(&a.ctl->cc_changed[round & 3]) != 0;
         __syncthreads();
         if (!sm.changed) {
@@ -119,7 +121,7 @@ __global__ void __launch_bounds__(CC_BLOCK) k_cc_persistent(CcArgs a) {
             return;
         }
         jump_phase(a);
-        if (!grid_barrier(a.ctl, a.timeout_ns)) return;
+        if (!flag_barrier(bar)) return;
     }
 }
 
@@ -135,6 +137,7 @@ grx_status grx_cc_launch(grx_graph *g, int32_t *label, const grx_opts *o, cudaSt
     a.n_active = g->n_active;
     a.label = label;
     a.ctl = g->ctl;
+    a.bar_flags = g->bar_flags;
     a.timeout_ns = grx_timeout_ns(o);
     static int per_sm = -1;
     if (per_sm < 0) {
@@ -142,8 +145,10 @@ grx_status grx_cc_launch(grx_graph *g, int32_t *label, const grx_opts *o, cudaSt
         if (per_sm < 1) return grx_fail(GRX_ECUDA, "cc: persistent kernel does not fit on an SM");
     }
     int max_grid = per_sm * g->ctx->num_sms;
+    if (max_grid > GRX_MAX_GRID) max_grid = GRX_MAX_GRID;
     int blocks = o->grid_blocks > 0 && o->grid_blocks < max_grid ? o->grid_blocks : max_grid;
-    GRX_CUDA(cudaMemsetAsync(&g->ctl->bar_count, 0, sizeof(unsigned int), s));
+    GRX_CUDA(cudaMemsetAsync(g->bar_flags, 0, sizeof(unsigned int) * (size_t)blocks, s));
+    GRX_CUDA(cudaMemsetAsync(&g->ctl->bar_release, 0, sizeof(unsigned int), s));
     void *args[] = {(void *)&a};
     GRX_CUDA(cudaLaunchCooperativeKernel((const void *)k_cc_persistent, dim3(blocks), dim3(CC_BLOCK),
                                          args, 0, s));

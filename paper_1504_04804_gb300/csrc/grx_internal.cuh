@@ -39,7 +39,13 @@ struct alignas(128) TravCtl {
     double pr_dangling[3];
     unsigned int flags;              // misc device flags (e.g. CC "changed")
     unsigned int cc_changed[4];
+    unsigned int pad3[26];
+    unsigned int bar_release;        // flag-barrier release word (own line)
+    unsigned int pad4[31];
 };
+
+// Maximum grid of the persistent kernels (size of the barrier flag array).
+#define GRX_MAX_GRID 4096
 
 struct DevStats {                    // device mirror of grx_trav_stats
     int32_t levels;
@@ -48,6 +54,7 @@ struct DevStats {                    // device mirror of grx_trav_stats
     unsigned long long edges_examined[GRX_MAX_LEVELS_STATS];
     unsigned long long vertices_scanned[GRX_MAX_LEVELS_STATS];
     unsigned long long discovered[GRX_MAX_LEVELS_STATS];
+    unsigned long long level_t0[GRX_MAX_LEVELS_STATS + 1];   // globaltimer at level start
 };
 
 struct grx_graph {
@@ -73,8 +80,10 @@ struct grx_graph {
     uint32_t *fbits[3];              // frontier bitmaps [words] each
     int32_t *qv[3];                  // frontier vertices [nv] each
     uint32_t *qe[3];                 // exclusive edge prefix per frontier slot
+    void *qr[3];                     // row start (OffT) per frontier slot
     int32_t *ulist[2];               // unvisited lists [nv] each
     TravCtl *ctl;
+    unsigned int *bar_flags;         // [GRX_MAX_GRID] per-block arrival flags
     DevStats *stats;
     // SSSP
     int32_t *stamp;                  // [nv] round in which v was last queued
@@ -196,6 +205,129 @@ __device__ __forceinline__ bool grid_barrier(TravCtl *ctl, unsigned long long ti
     return s_ok != 0;
 }
 
+// Flag-based grid barrier: block b (> 0) publishes its arrival in flags[b];
+// block 0's threads gather all flags in parallel, then release everyone with
+// one word.  No contended atomic.  `gen` counts barriers within a launch
+// (flags and release word are zeroed before the launch, gen starts at 0).
+// Every wait is bounded by timeout_ns; a block that gives up records
+// GRX_ETIMEOUT and returns false.
+struct FlagBarrier {
+    unsigned int *flags;
+    unsigned int *release;
+    TravCtl *ctl;
+    unsigned long long timeout_ns;
+    unsigned int gen;
+};
+
+__device__ __forceinline__ bool flag_barrier(FlagBarrier &b) {
+    __shared__ int s_ok;
+    const unsigned int gen = ++b.gen;
+    __syncthreads();
+    if (blockIdx.x == 0) {
+        int ok = 1;
+        for (unsigned int i = threadIdx.x + 1; i < gridDim.x && ok; i += blockDim.x) {
+            if (ld_acquire_u32(b.flags + i) == gen) continue;
+            const unsigned long long t0 = grx_globaltimer();
+            while (ld_acquire_u32(b.flags + i) != gen) {
+                if (grx_globaltimer() - t0 > b.timeout_ns) { ok = 0; break; }
+                __nanosleep(32);
+            }
+        }
+        ok = __syncthreads_and(ok);
+        if (threadIdx.x == 0) {
+            if (ok) {
+                __threadfence();
+                st_release_u32(b.release, gen);
+            } else {
+                grx_set_status(b.ctl, GRX_ETIMEOUT);
+            }
+            s_ok = ok;
+        }
+    } else if (threadIdx.x == 0) {
+        int ok = 1;
+        __threadfence();
+        st_release_u32(b.flags + blockIdx.x, gen);
+        if (ld_acquire_u32(b.release) != gen) {
+            const unsigned long long t0 = grx_globaltimer();
+            while (ld_acquire_u32(b.release) != gen) {
+                if (grx_globaltimer() - t0 > b.timeout_ns) {
+                    grx_set_status(b.ctl, GRX_ETIMEOUT);
+                    ok = 0;
+                    break;
+                }
+                __nanosleep(32);
+            }
+        }
+        __threadfence();
+        s_ok = ok;
+    }
+    __syncthreads();
+    return s_ok != 0;
+}
+
+// Warp-aggregated append of up to N items per lane (bit k of mask = item k
+// present) to a frontier whose counter packs (count << 32 | edge total).  One
+// atomic per warp; the edge prefix stays monotone in position order.  Must be
+// called by all 32 lanes.
+template <int N, typename OffT>
+__device__ __forceinline__ void warp_append_items(const int32_t (&v)[N], const uint32_t (&deg)[N],
+                                                  const OffT (&rs)[N], uint32_t mask, int32_t *qv,
+                                                  uint32_t *qe, OffT *qr, unsigned long long *ctr) {
+    uint32_t cnt = __popc(mask), dsum = 0;
+#pragma unroll
+    for (int k = 0; k < N; ++k)
+        if (mask >> k & 1u) dsum += deg[k];
+    const unsigned int lane = threadIdx.x & 31;
+    uint32_t c = cnt, s = dsum;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        uint32_t c2 = __shfl_up_sync(0xffffffffu, c, o);
+        uint32_t s2 = __shfl_up_sync(0xffffffffu, s, o);
+        if (lane >= (unsigned)o) { c += c2; s += s2; }
+    }
+    const uint32_t tc = __shfl_sync(0xffffffffu, c, 31);
+    if (tc == 0) return;
+    const uint32_t ts = __shfl_sync(0xffffffffu, s, 31);
+    unsigned long long base = 0;
+    if (lane == 31) base = atomicAdd(ctr, ((unsigned long long)tc << 32) | (unsigned long long)ts);
+    base = __shfl_sync(0xffffffffu, base, 31);
+    uint32_t pos = (uint32_t)(base >> 32) + c - cnt;
+    uint32_t eo = (uint32_t)base + s - dsum;
+#pragma unroll
+    for (int k = 0; k < N; ++k) {
+        if (mask >> k & 1u) {
+            qv[pos] = v[k];
+            qe[pos] = eo;
+            if (qr) qr[pos] = rs[k];
+            ++pos;
+            eo += deg[k];
+        }
+    }
+}
+
+// Warp-aggregated append of up to N list items per lane with a 32-bit counter.
+template <int N>
+__device__ __forceinline__ void warp_append_list_items(const int32_t (&v)[N], uint32_t mask,
+                                                       int32_t *list, unsigned int *ctr) {
+    const unsigned int lane = threadIdx.x & 31;
+    const uint32_t cnt = __popc(mask);
+    uint32_t c = cnt;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const uint32_t c2 = __shfl_up_sync(0xffffffffu, c, o);
+        if (lane >= (unsigned)o) c += c2;
+    }
+    const uint32_t tc = __shfl_sync(0xffffffffu, c, 31);
+    if (tc == 0) return;
+    unsigned int base = 0;
+    if (lane == 31) base = atomicAdd(ctr, tc);
+    base = __shfl_sync(0xffffffffu, base, 31);
+    uint32_t pos = base + c - cnt;
+#pragma unroll
+    for (int k = 0; k < N; ++k)
+        if (mask >> k & 1u) list[pos++] = v[k];
+}
+
 __device__ __forceinline__ unsigned int lane_id() { return threadIdx.x & 31; }
 
 __device__ __forceinline__ unsigned int lanemask_lt() {
@@ -276,6 +408,54 @@ __device__ __forceinline__ int upper_index_smem(const uint32_t *a, int n, uint32
         if (a[mid] <= key) lo = mid; else hi = mid;
     }
     return lo;
+}
+
+// Largest i in [0, n) with a[i] <= key (a ascending, a[0] <= key), found by
+// one full warp with a 32-ary search: each round probes 32 points at once, so
+// the dependent round trips are log32(n).  All 32 lanes get the result.
+__device__ __forceinline__ int64_t warp_upper_index_cg(const uint32_t *a, int64_t n, uint32_t key) {
+    const unsigned int lane = threadIdx.x & 31;
+    int64_t lo = 0, hi = n;
+    while (hi - lo > 1) {
+        const int64_t step = (hi - lo + 31) / 32;
+        const int64_t idx = lo + (int64_t)lane * step;
+        const bool ok = idx < hi && __ldcg(a + idx) <= key;
+        const unsigned int m = __ballot_sync(0xffffffffu, ok);
+        const int last = 31 - __clz(m);
+        lo = lo + (int64_t)last * step;
+        hi = min(hi, lo + step);
+    }
+    return lo;
+}
+
+// Block-wide exclusive scan of three counters (blockDim.x == NT, a multiple
+// of 32).  Returns the exclusive prefixes and, in every thread, the totals.
+template <int NT>
+__device__ __forceinline__ void block_scan3(uint32_t a, uint32_t b, uint32_t c, uint32_t &ea,
+                                            uint32_t &eb, uint32_t &ec, uint32_t &ta, uint32_t &tb,
+                                            uint32_t &tc) {
+    __shared__ uint32_t ws[3][NT / 32];
+    const unsigned int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    uint32_t x = a, y = b, z = c;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        uint32_t x2 = __shfl_up_sync(0xffffffffu, x, o);
+        uint32_t y2 = __shfl_up_sync(0xffffffffu, y, o);
+        uint32_t z2 = __shfl_up_sync(0xffffffffu, z, o);
+        if (lane >= (unsigned)o) { x += x2; y += y2; z += z2; }
+    }
+    if (lane == 31) { ws[0][wid] = x; ws[1][wid] = y; ws[2][wid] = z; }
+    __syncthreads();
+    uint32_t px = 0, py = 0, pz = 0, sx = 0, sy = 0, sz = 0;
+#pragma unroll
+    for (int w = 0; w < NT / 32; ++w) {
+        const uint32_t wx = ws[0][w], wy = ws[1][w], wz = ws[2][w];
+        if ((unsigned)w < wid) { px += wx; py += wy; pz += wz; }
+        sx += wx; sy += wy; sz += wz;
+    }
+    ea = px + x - a; eb = py + y - b; ec = pz + z - c;
+    ta = sx; tb = sy; tc = sz;
+    __syncthreads();
 }
 
 template <typename T>

@@ -7,7 +7,8 @@
 //
 // Same persistent, load-balanced structure as the push step of BFS: the
 // frontier's edges are cut into equal tiles using the degree prefix that the
-// append atomic produced; rounds are separated by a bounded grid barrier.
+// append atomic produced, each thread keeps a run of SS_ITEMS edges' loads and
+// atomics in flight, and rounds are separated by a bounded grid barrier.
 #include "grx_internal.cuh"
 
 namespace {
@@ -27,6 +28,7 @@ struct SsspArgs {
     int32_t *Q[3];
     uint32_t *E[3];
     TravCtl *ctl;
+    unsigned int *bar_flags;
     DevStats *stats;
     unsigned long long timeout_ns;
     int32_t src;
@@ -78,29 +80,80 @@ __device__ void relax_round(const SsspArgs<OffT> &a, int L, uint32_t q, uint64_t
             sm.du[j] = __ldcg(a.dist + u);
         }
         __syncthreads();
-#pragma unroll 2
+        // a run of SS_ITEMS consecutive edges per thread, all loads in flight together
+        const uint64_t t0 = e0 + (uint64_t)threadIdx.x * SS_ITEMS;
+        int32_t v[SS_ITEMS];
+        uint32_t nd[SS_ITEMS];
+        uint32_t valid = 0;
+#pragma unroll
         for (int k = 0; k < SS_ITEMS; ++k) {
-            const uint64_t e = e0 + (uint64_t)(k * SS_BLOCK + threadIdx.x);
-            bool queued = false;
-            int32_t v = 0;
-            uint32_t deg = 0;
-            if (e < e1) {
-                int j = upper_index_smem(sm.qe, n, (uint32_t)e);
-                const OffT idx = sm.rs[j] + (OffT)((uint32_t)e - sm.qe[j]);
-                v = __ldg(a.col + idx);
-                const uint64_t nd = (uint64_t)sm.du[j] + __ldg(a.w + idx);
-                if (nd >= 0xffffffffull) {
-                    grx_set_status(a.ctl, GRX_ERANGE);
-                } else if ((uint32_t)nd < __ldcg(a.dist + v)) {
-                    uint32_t old = atomicMin(a.dist + v, (uint32_t)nd);
-                    if ((uint32_t)nd < old && atomicExch(a.stamp + v, L + 1) != L + 1) {
-                        queued = true;
-                        deg = (uint32_t)(__ldg(a.ro + v + 1) - __ldg(a.ro + v));
+            v[k] = 0;
+            nd[k] = 0xffffffffu;
+        }
+        if (t0 < e1) {
+            int j = upper_index_smem(sm.qe, n, (uint32_t)t0);
+            uint32_t wt[SS_ITEMS];
+            uint32_t du[SS_ITEMS];
+#pragma unroll
+            for (int k = 0; k < SS_ITEMS; ++k) {
+                const uint64_t e = t0 + k;
+                wt[k] = 0;
+                du[k] = 0xffffffffu;
+                if (e < e1) {
+                    while (j + 1 < n && sm.qe[j + 1] <= (uint32_t)e) ++j;
+                    const OffT idx = sm.rs[j] + (OffT)((uint32_t)e - sm.qe[j]);
+                    v[k] = __ldg(a.col + idx);
+                    wt[k] = __ldg(a.w + idx);
+                    du[k] = sm.du[j];
+                    valid |= 1u << k;
+                }
+            }
+#pragma unroll
+            for (int k = 0; k < SS_ITEMS; ++k) {
+                if (valid >> k & 1u) {
+                    const uint64_t s64 = (uint64_t)du[k] + wt[k];
+                    if (s64 >= 0xffffffffull) {
+                        grx_set_status(a.ctl, GRX_ERANGE);
+                        valid &= ~(1u << k);
+                    } else {
+                        nd[k] = (uint32_t)s64;
                     }
                 }
             }
-            warp_append_frontier(queued && deg > 0, v, deg, Qv_out, Qe_out, ctr);
         }
+        uint32_t cur[SS_ITEMS];
+#pragma unroll
+        for (int k = 0; k < SS_ITEMS; ++k) cur[k] = (valid >> k & 1u) ? __ldcg(a.dist + v[k]) : 0u;
+        uint32_t improved = 0;
+#pragma unroll
+        for (int k = 0; k < SS_ITEMS; ++k) {
+            if ((valid >> k & 1u) && nd[k] < cur[k]) {
+                const uint32_t old = atomicMin(a.dist + v[k], nd[k]);
+                if (nd[k] < old) improved |= 1u << k;
+            }
+        }
+        uint32_t queued = 0;
+#pragma unroll
+        for (int k = 0; k < SS_ITEMS; ++k)
+            if ((improved >> k & 1u) && atomicExch(a.stamp + v[k], L + 1) != L + 1) queued |= 1u << k;
+        uint32_t deg[SS_ITEMS];
+        OffT rb[SS_ITEMS], re[SS_ITEMS];
+#pragma unroll
+        for (int k = 0; k < SS_ITEMS; ++k) {
+            rb[k] = 0;
+            re[k] = 0;
+            if (queued >> k & 1u) {
+                rb[k] = __ldg(a.ro + v[k]);
+                re[k] = __ldg(a.ro + v[k] + 1);
+            }
+        }
+        uint32_t app = 0;
+#pragma unroll
+        for (int k = 0; k < SS_ITEMS; ++k) {
+            deg[k] = (uint32_t)(re[k] - rb[k]);
+            if ((queued >> k & 1u) && deg[k]) app |= 1u << k;
+        }
+        warp_append_items<SS_ITEMS, OffT>(v, deg, rb, app, Qv_out, Qe_out, (OffT *)nullptr, ctr);
         __syncthreads();
     }
     if (STATS && blockIdx.x == 0 && threadIdx.x == 0 && L < GRX_MAX_LEVELS_STATS) {
@@ -115,6 +168,7 @@ __device__ void relax_round(const SsspArgs<OffT> &a, int L, uint32_t q, uint64_t
 template <typename OffT, bool STATS>
 __global__ void __launch_bounds__(SS_BLOCK) k_sssp_persistent(SsspArgs<OffT> a) {
     __shared__ SsspSmem<OffT> sm;
+    FlagBarrier bar{a.bar_flags, &a.ctl->bar_release, a.ctl, a.timeout_ns, 0u};
     if (threadIdx.x == 0) {
         uint32_t deg = (uint32_t)(a.ro[a.src + 1] - a.ro[a.src]);
         sm.q = deg ? 1u : 0u;
@@ -127,9 +181,12 @@ __global__ void __launch_bounds__(SS_BLOCK) k_sssp_persistent(SsspArgs<OffT> a) 
         const uint32_t q = sm.q;
         const uint32_t T = sm.T;
         if (sm.done) break;
-        if (blockIdx.x == 0 && threadIdx.x == 0) a.ctl->qpack[(L + 2) & 3] = 0ull;
+        if (blockIdx.x == 0 && threadIdx.x == 0) {
+            a.ctl->qpack[(L + 2) & 3] = 0ull;
+            if (STATS && L < GRX_MAX_LEVELS_STATS) a.stats->level_t0[L] = grx_globaltimer();
+        }
         relax_round<OffT, STATS>(a, L, q, T, sm);
-        if (!grid_barrier(a.ctl, a.timeout_ns)) break;
+        if (!flag_barrier(bar)) return;
         if (threadIdx.x == 0) {
             unsigned long long pk = ld_relaxed_u64(&a.ctl->qpack[(L + 1) & 3]);
             sm.q = (uint32_t)(pk >> 32);
@@ -139,7 +196,10 @@ __global__ void __launch_bounds__(SS_BLOCK) k_sssp_persistent(SsspArgs<OffT> a) 
         }
         __syncthreads();
     }
-    if (blockIdx.x == 0 && threadIdx.x == 0) a.ctl->levels_run = L;
+    if (blockIdx.x == 0 && threadIdx.x == 0) {
+        a.ctl->levels_run = L;
+        if (STATS && L <= GRX_MAX_LEVELS_STATS) a.stats->level_t0[L] = grx_globaltimer();
+    }
 }
 
 __global__ void k_sssp_init(int32_t src, const void *ro, int off64, uint32_t *dist, int32_t *Q0,
@@ -171,6 +231,7 @@ grx_status launch_typed(grx_graph *g, int32_t src, uint32_t *dist, const grx_opt
         a.E[i] = g->qe[i];
     }
     a.ctl = g->ctl;
+    a.bar_flags = g->bar_flags;
     a.stats = g->stats;
     a.timeout_ns = grx_timeout_ns(o);
     a.src = src;
@@ -181,7 +242,10 @@ grx_status launch_typed(grx_graph *g, int32_t src, uint32_t *dist, const grx_opt
         if (per_sm < 1) return grx_fail(GRX_ECUDA, "sssp: persistent kernel does not fit on an SM");
     }
     int max_grid = per_sm * g->ctx->num_sms;
+    if (max_grid > GRX_MAX_GRID) max_grid = GRX_MAX_GRID;
     int blocks = o->grid_blocks > 0 && o->grid_blocks < max_grid ? o->grid_blocks : max_grid;
+    GRX_CUDA(cudaMemsetAsync(g->bar_flags, 0, sizeof(unsigned int) * (size_t)blocks, s));
+    GRX_CUDA(cudaMemsetAsync(&g->ctl->bar_release, 0, sizeof(unsigned int), s));
     void *args[] = {(void *)&a};
     if (o->ev_begin) GRX_CUDA(cudaEventRecord((cudaEvent_t)o->ev_begin, s));
     GRX_CUDA(cudaLaunchCooperativeKernel((const void *)k_sssp_persistent<OffT, STATS>, dim3(blocks),

@@ -38,7 +38,8 @@ class grx_opts(ctypes.Structure):
     _fields_ = [("direction", ctypes.c_int), ("alpha", ctypes.c_float), ("beta", ctypes.c_float),
                 ("loop", ctypes.c_int), ("grid_blocks", ctypes.c_int),
                 ("block_threads", ctypes.c_int), ("timeout_s", ctypes.c_double),
-                ("collect_stats", ctypes.c_int), ("ev_begin", ctypes.c_void_p),
+                ("collect_stats", ctypes.c_int), ("exact_fv", ctypes.c_int),
+                ("ev_begin", ctypes.c_void_p),
                 ("ev_end", ctypes.c_void_p)]
 
 
@@ -48,7 +49,8 @@ class grx_trav_stats(ctypes.Structure):
                 ("frontier", ctypes.c_int64 * GRX_MAX_LEVELS_STATS),
                 ("edges_examined", ctypes.c_int64 * GRX_MAX_LEVELS_STATS),
                 ("vertices_scanned", ctypes.c_int64 * GRX_MAX_LEVELS_STATS),
-                ("discovered", ctypes.c_int64 * GRX_MAX_LEVELS_STATS)]
+                ("discovered", ctypes.c_int64 * GRX_MAX_LEVELS_STATS),
+                ("level_ns", ctypes.c_int64 * GRX_MAX_LEVELS_STATS)]
 
 
 _ALLOC_FN = ctypes.CFUNCTYPE(ctypes.c_void_p, ctypes.c_size_t, ctypes.c_void_p, ctypes.c_void_p)
@@ -327,7 +329,8 @@ def last_stats(g: Graph, stream=None) -> dict:
             "frontier": list(st.frontier[:n]),
             "edges_examined": list(st.edges_examined[:n]),
             "vertices_scanned": list(st.vertices_scanned[:n]),
-            "discovered": list(st.discovered[:n])}
+            "discovered": list(st.discovered[:n]),
+            "level_ns": list(st.level_ns[:n])}
 
 
 def as_uint32(t: torch.Tensor) -> np.ndarray:

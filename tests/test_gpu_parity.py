@@ -75,10 +75,11 @@ def test_bfs_matches_oracle(grx, loaded, name, mode):
         assert oracle.check_bfs(g.row_offsets, g.col_indices, s, got, p.cpu().numpy()) == 0
 
 
-@pytest.mark.parametrize("alpha,beta", [(0.01, 0.1), (1e-4, 1e-3), (0.5, 0.05), (1e-6, 10.0)])
-def test_dobfs_independent_of_switch_parameters(grx, loaded, alpha, beta):
+@pytest.mark.parametrize("alpha,beta,exact", [(0.01, 0.1, 0), (1e-4, 1e-3, 0), (0.5, 0.05, 0),
+                                              (1e-6, 10.0, 0), (0.01, 0.1, 1), (0.2, 0.5, 1)])
+def test_dobfs_independent_of_switch_parameters(grx, loaded, alpha, beta, exact):
     g, dg = GRAPHS["rmat13"], loaded["rmat13"]
-    o = grx.opts(alpha=alpha, beta=beta, collect_stats=1)
+    o = grx.opts(alpha=alpha, beta=beta, exact_fv=exact, collect_stats=1)
     for s in _sources(g, 3, seed=4):
         d = grx.bfs(dg, s, opts=o)
         st = grx.last_stats(dg)
