@@ -138,12 +138,27 @@ void grx_opts_default(grx_opts *o);
 grx_status bfs(grx_graph *g, int32_t src, int32_t *depth_out, int32_t *parent_out,
                const grx_opts *opts, void *stream);
 
+/* bfs_multi -- up to 64 BFS sources in one traversal that shares the edge
+ * stream: every vertex carries 64-bit frontier / seen lane masks and lane b
+ * starts at srcs_host[b] (host array).  depth_out: device int32[n][nv]
+ * (lane-major), lane b equal to bfs(srcs_host[b]).  n in 1..64; duplicate
+ * sources allowed.  opts->direction, alpha, beta act on lane popcounts. */
+grx_status bfs_multi(grx_graph *g, const int32_t *srcs_host, int n, int32_t *depth_out,
+                     const grx_opts *opts, void *stream);
+
 /* sssp -- Table 1 SSSP: frontier label-correcting relaxation with atomicMin
  * (the paper's min combiner, Sec. 3) until no distance improves.
  * dist_out: device uint32[nv], UINT32_MAX if unreached.  Needs weights
  * (else GRX_EINVAL).  A distance >= UINT32_MAX sets GRX_ERANGE status. */
 grx_status sssp(grx_graph *g, int32_t src, uint32_t *dist_out,
                 const grx_opts *opts, void *stream);
+
+/* sssp_multi -- up to 64 SSSP sources sharing one edge stream (per lane the
+ * result of sssp()).  dist_out: device uint32[n][nv] (lane-major),
+ * UINT32_MAX if unreached.  Needs weights.  Uses 256 bytes of workspace per
+ * vertex (distances are kept vertex-major inside the library). */
+grx_status sssp_multi(grx_graph *g, const int32_t *srcs_host, int n, uint32_t *dist_out,
+                      const grx_opts *opts, void *stream);
 
 /* cc -- Table 1 CC (Soman et al.'s hooking + pointer jumping).  label_out:
  * device int32[nv], the minimum vertex id of the vertex's component. */

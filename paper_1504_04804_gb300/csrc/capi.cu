@@ -336,10 +336,10 @@ grx_status grx_ensure_ms_workspace(grx_graph *g, cudaStream_t s) {
     if (st != GRX_OK) return st;
     if (g->ms_ready) return GRX_OK;
     const size_t b = (size_t)g->nv * 8;
-    g->ms_cur = (unsigned long long *)grx_alloc(g, b, s);
+    for (int i = 0; i < 3; ++i) g->ms_cur[i] = (unsigned long long *)grx_alloc(g, b, s);
     g->ms_next = (unsigned long long *)grx_alloc(g, b, s);
     g->ms_seen = (unsigned long long *)grx_alloc(g, b, s);
-    if (!g->ms_cur || !g->ms_next || !g->ms_seen)
+    if (!g->ms_cur[0] || !g->ms_cur[1] || !g->ms_cur[2] || !g->ms_next || !g->ms_seen)
         return grx_fail(GRX_ENOMEM, "multi-source workspace allocation failed (nv=%d)", g->nv);
     g->ms_ready = 1;
     return GRX_OK;
@@ -447,3 +447,41 @@ extern "C" grx_status pagerank(grx_graph *g, float damping, int iters, float *ra
     return grx_pr_launch(g, damping, iters, rank_out, (cudaStream_t)stream);
 }
 
+
+static grx_status check_sources(grx_graph *g, const int32_t *srcs, int n, const char *who) {
+    if (!srcs) return grx_fail(GRX_EINVAL, "%s: srcs is NULL", who);
+    if (n < 1 || n > 64) return grx_fail(GRX_EINVAL, "%s: n must be in 1..64 (got %d)", who, n);
+    for (int i = 0; i < n; ++i)
+        if (srcs[i] < 0 || srcs[i] >= g->nv)
+            return grx_fail(GRX_EINVAL, "%s: source %d (lane %d) out of range", who, srcs[i], i);
+    return GRX_OK;
+}
+
+extern "C" grx_status bfs_multi(grx_graph *g, const int32_t *srcs_host, int n, int32_t *depth_out,
+                                const grx_opts *opts, void *stream) {
+    grx_status st = check_graph(g, "bfs_multi");
+    if (st) return st;
+    if ((st = check_sources(g, srcs_host, n, "bfs_multi"))) return st;
+    if (!depth_out) return grx_fail(GRX_EINVAL, "bfs_multi: depth_out is NULL");
+    grx_opts o;
+    grx_resolve_opts(opts, &o);
+    if (o.direction < GRX_DIR_AUTO || o.direction > GRX_DIR_PULL)
+        return grx_fail(GRX_EINVAL, "bfs_multi: bad direction %d", o.direction);
+    g->last_stream = stream;
+    if ((st = grx_ensure_ms_workspace(g, (cudaStream_t)stream))) return st;
+    return grx_msbfs_launch(g, srcs_host, n, depth_out, &o, (cudaStream_t)stream);
+}
+
+extern "C" grx_status sssp_multi(grx_graph *g, const int32_t *srcs_host, int n, uint32_t *dist_out,
+                                 const grx_opts *opts, void *stream) {
+    grx_status st = check_graph(g, "sssp_multi");
+    if (st) return st;
+    if (!g->w) return grx_fail(GRX_EINVAL, "sssp_multi: graph has no weights");
+    if ((st = check_sources(g, srcs_host, n, "sssp_multi"))) return st;
+    if (!dist_out) return grx_fail(GRX_EINVAL, "sssp_multi: dist_out is NULL");
+    grx_opts o;
+    grx_resolve_opts(opts, &o);
+    g->last_stream = stream;
+    if ((st = grx_ensure_ms_workspace(g, (cudaStream_t)stream))) return st;
+    return grx_mssp_launch(g, srcs_host, n, dist_out, &o, (cudaStream_t)stream);
+}

@@ -42,6 +42,7 @@ struct alignas(128) TravCtl {
     unsigned int pad3[26];
     unsigned int bar_release;        // flag-barrier release word (own line)
     unsigned int pad4[31];
+    unsigned long long pairs[4];     // multi-source: (vertex, lane) pairs discovered, ring
 };
 
 // Maximum grid of the persistent kernels (size of the barrier flag array).
@@ -93,7 +94,8 @@ struct grx_graph {
     int32_t *pr_fix;                 // per-tile row needing a fix-up
     int64_t pr_fix_len;
     // multi-source
-    unsigned long long *ms_cur, *ms_next, *ms_seen;   // [nv] each
+    unsigned long long *ms_cur[3], *ms_next, *ms_seen;   // [nv] each
+    uint32_t *ms_dist;               // batched SSSP, vertex-major [nv][64]
     int ms_ready;
     // bookkeeping for frees
     struct Alloc { void *p; size_t n; } allocs[48];
@@ -118,6 +120,11 @@ grx_status grx_cuda_fail(cudaError_t e, const char *what);
 
 // Builds g->active / g->aoff / g->n_active (synchronises s once).
 grx_status grx_build_active(grx_graph *g, cudaStream_t s);
+
+grx_status grx_msbfs_launch(grx_graph *g, const int32_t *srcs, int n, int32_t *depth,
+                            const grx_opts *o, cudaStream_t s);
+grx_status grx_mssp_launch(grx_graph *g, const int32_t *srcs, int n, uint32_t *dist,
+                           const grx_opts *o, cudaStream_t s);
 
 // Options resolution.
 void grx_resolve_opts(const grx_opts *in, grx_opts *out);

@@ -77,6 +77,8 @@ SIGNATURES = [
     ("cc", _I, [_P, _P, _P]),
     ("pagerank", _I, [_P, ctypes.c_float, _I, _P, _P]),
     ("grx_last_stats", _I, [_P, _P, _P]),
+    ("bfs_multi", _I, [_P, _P, _I, _P, _P, _P]),
+    ("sssp_multi", _I, [_P, _P, _I, _P, _P, _P]),
     ("bfs_noalloc", _I, [_I64, _I64, _P, _P, ctypes.c_int32, _P, _P, _P, _P, _P]),
     ("grx_rmat_edges", _I, [_I, _I64, _U64, _U64, _U64, _U64, _P, _P, _P]),
     ("grx_edge_weights", _I, [_I64, _I64, _P, _P, ctypes.c_uint32, _U64, _P, _P]),
@@ -277,6 +279,31 @@ def sssp(g: Graph, src: int, dist_out=None, opts: grx_opts | None = None, stream
     _check(lib().sssp(g.handle, int(src), d.data_ptr(),
                       ctypes.byref(opts) if opts is not None else None, _stream_ptr(stream)), "sssp")
     return d
+
+
+def _srcs_arg(srcs):
+    arr = np.ascontiguousarray(np.asarray(srcs, dtype=np.int32))
+    return arr, arr.ctypes.data_as(ctypes.c_void_p), int(arr.shape[0])
+
+
+def bfs_multi(g: Graph, srcs, depth_out=None, opts: grx_opts | None = None, stream=None):
+    """Depths of up to 64 sources in one traversal: int32 [n, nv] (lane-major)."""
+    arr, p, n = _srcs_arg(srcs)
+    d = _out(depth_out, n * g.nv, torch.int32, g.device)
+    _check(lib().bfs_multi(g.handle, p, n, d.data_ptr(),
+                           ctypes.byref(opts) if opts is not None else None, _stream_ptr(stream)),
+           "bfs_multi")
+    return d[: n * g.nv].view(n, g.nv)
+
+
+def sssp_multi(g: Graph, srcs, dist_out=None, opts: grx_opts | None = None, stream=None):
+    """Distances of up to 64 sources, int32 tensor [n, nv] holding uint32 bits."""
+    arr, p, n = _srcs_arg(srcs)
+    d = _out(dist_out, n * g.nv, torch.int32, g.device)
+    _check(lib().sssp_multi(g.handle, p, n, d.data_ptr(),
+                            ctypes.byref(opts) if opts is not None else None, _stream_ptr(stream)),
+           "sssp_multi")
+    return d[: n * g.nv].view(n, g.nv)
 
 
 def cc(g: Graph, label_out=None, stream=None):

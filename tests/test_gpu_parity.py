@@ -244,3 +244,63 @@ def test_timeout_status_is_reported_and_context_survives(grx, loaded):
     d = grx.bfs(dg, 0)
     grx.graph_status(dg)
     assert np.array_equal(d.cpu().numpy(), oracle.bfs(g.row_offsets, g.col_indices, 0))
+
+
+@pytest.mark.parametrize("name", ["rmat10", "rmat13", "rmat14_ef4", "grid64", "path", "star", "disconnected"])
+@pytest.mark.parametrize("mode", list(MODES))
+def test_bfs_multi_lanes_match_oracle(grx, loaded, name, mode):
+    g, dg = GRAPHS[name], loaded[name]
+    srcs = _sources(g, 61, seed=7) if name != "disconnected" else [1, 5, 10, 30, 0, 2]
+    srcs = (srcs + [srcs[0], g.nv - 1, srcs[-1]])[:64]          # duplicates and an isolated/last vertex
+    d = grx.bfs_multi(dg, srcs, opts=grx.opts(direction=MODES[mode])).cpu().numpy()
+    grx.graph_status(dg)
+    for b, s in enumerate(srcs):
+        assert np.array_equal(d[b], oracle.bfs(g.row_offsets, g.col_indices, s)), (name, mode, b, s)
+
+
+def test_bfs_multi_few_lanes_and_stats(grx, loaded):
+    g, dg = GRAPHS["rmat13"], loaded["rmat13"]
+    for n in (1, 2, 31, 33):
+        srcs = _sources(g, n, seed=n)
+        d = grx.bfs_multi(dg, srcs, opts=grx.opts(collect_stats=1)).cpu().numpy()
+        st = grx.last_stats(dg)
+        want = [oracle.bfs(g.row_offsets, g.col_indices, s) for s in srcs]
+        for b in range(n):
+            assert np.array_equal(d[b], want[b])
+        # discovered (vertex, lane) pairs per level equal the oracle's level sizes summed over lanes
+        total = sum(int((w >= 0).sum()) for w in want)
+        assert sum(st["discovered"]) + n == total
+
+
+@pytest.mark.parametrize("name", ["rmat10", "rmat13", "rmat14_ef4", "grid64", "path", "star", "disconnected"])
+def test_sssp_multi_lanes_match_oracle(grx, loaded, name):
+    g, dg = GRAPHS[name], loaded[name]
+    srcs = _sources(g, 40, seed=3) if name != "disconnected" else [1, 5, 10, 30, 0]
+    srcs = srcs + [srcs[0], g.nv - 1]
+    d = grx.sssp_multi(dg, srcs).cpu().numpy().view(np.uint32)
+    grx.graph_status(dg)
+    for b, s in enumerate(srcs):
+        want = oracle.sssp(g.row_offsets, g.col_indices, g.weights, s)
+        assert np.array_equal(d[b], want), (name, b, s)
+
+
+def test_multi_source_on_the_6_vertex_union(grx):
+    pairs = list(itertools.combinations(range(6), 2))
+    edges = []
+    for gi in range(1 << 15):
+        base = 6 * gi
+        edges += [(base + a, base + b) for i, (a, b) in enumerate(pairs) if gi >> i & 1]
+    u = inputs.csr_from_edges(6 << 15, edges)
+    rows = np.repeat(np.arange(u.nv), np.diff(u.row_offsets))
+    lo = np.minimum(rows, u.col_indices).astype(np.uint64)
+    hi = np.maximum(rows, u.col_indices).astype(np.uint64)
+    u.weights = (1 + inputs.draw(67, lo * np.uint64(u.nv) + hi) % np.uint64(3)).astype(np.uint32)
+    du = grx.load(u)
+    rng = np.random.default_rng(9)
+    for rep in range(3):
+        srcs = [int(6 * gi + rng.integers(0, 6)) for gi in rng.choice(1 << 15, size=64, replace=False)]
+        d = grx.bfs_multi(du, srcs).cpu().numpy()
+        dist = grx.sssp_multi(du, srcs).cpu().numpy().view(np.uint32)
+        for b, s in enumerate(srcs):
+            assert np.array_equal(d[b], oracle.bfs(u.row_offsets, u.col_indices, s))
+            assert np.array_equal(dist[b], oracle.sssp(u.row_offsets, u.col_indices, u.weights, s))
