@@ -216,8 +216,7 @@ def _config(args, nv, ne, offsets):
                         f"(a,b,c,d=0.57,0.19,0.19,0.05, seed {cfg['seed']}), direction-optimising BFS "
                         f"from {N_SOURCES} seeded sources",
             "nv": nv, "ne_directed": ne, "offsets": offsets, "sources_per_step": N_SOURCES,
-            "l2": "flushed before every traversal (256 MiB write, untimed)",
-            "alpha": args.alpha, "beta": args.beta}
+            "l2": "flushed before every traversal (256 MiB write, untimed)"}
 
 
 # ---------------------------------------------------------------------------
@@ -233,6 +232,8 @@ def main():
     ap.add_argument("--cpu-budget", type=float, default=15.0,
                     help="seconds of oracle BFS for the cpu_baseline sample")
     ap.add_argument("--no-extra", action="store_true", help="skip SSSP/CC/PageRank timings")
+    ap.add_argument("--no-tune", action="store_true",
+                    help="use the paper's switch rule with --alpha/--beta instead of the autotuner")
     args = ap.parse_args()
     if args.impl == "reference":
         return reference_arm(args)
@@ -258,8 +259,17 @@ def main():
     srcs = [int(s) for s in inputs.pick_sources(ro_h, N_SOURCES, SOURCE_SEED)]
     deg_h = np.diff(ro_h)
 
+    # autotuned switch rule / alpha / beta / grid on separate tuning sources
+    # (seed 2, not the measured ones); tuning time is reported, not timed
+    tuned = None
+    knobs = {"alpha": args.alpha, "beta": args.beta, "exact_fv": 0, "grid_blocks": 0}
+    if not args.no_tune:
+        from paper_1504_04804_gb300 import autotune
+        tuned = autotune.tune_bfs(g, ro_h, cache=None)
+        knobs = {k: tuned[k] for k in ("alpha", "beta", "exact_fv", "grid_blocks")}
+
     # untimed instrumented pass: per-source byte model and TEPS numerator
-    st_opts = grx.opts(alpha=args.alpha, beta=args.beta, collect_stats=1)
+    st_opts = grx.opts(collect_stats=1, **knobs)
     per_src = {}
     for s in srcs:
         d = grx.bfs(g, s, opts=st_opts)
@@ -270,7 +280,7 @@ def main():
     grx.graph_status(g)
 
     flush = torch.empty(256 << 20, dtype=torch.uint8, device=f"cuda:{dev}")
-    o = grx.opts(alpha=args.alpha, beta=args.beta)
+    o = grx.opts(**knobs)
     depth = torch.empty(nv, dtype=torch.int32, device=f"cuda:{dev}")
     evs = [[torch.cuda.Event(enable_timing=True) for _ in range(4)]
            for _ in range(args.steps * len(srcs))]
@@ -368,7 +378,10 @@ def main():
             "steps": args.steps, "warmup": args.warmup,
             "ms_per_step": t_max / args.steps * 1e3, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "int32", "data": "synthetic",
-            "config": _config(args, nv, ne, "int32" if off_bytes == 4 else "int64"),
+            "config": dict(_config(args, nv, ne, "int32" if off_bytes == 4 else "int64"), **knobs),
+            "autotune": None if tuned is None else {
+                "seconds": tuned["seconds"], "configs_tried": tuned["tried"],
+                "tuning_sources": tuned["tuning_sources"]},
             "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                          "frac": achieved / peak, "traffic": None,
                          "kernel": "k_bfs_persistent", "peak_kind": peak_kind,

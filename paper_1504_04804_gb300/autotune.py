@@ -1,0 +1,136 @@
+"""Per-graph autotuner for the traversal knobs.
+
+Sec. 6.1 observes that the best direction-switch parameters (do_a, do_b) are
+consistent for graphs of a similar type; this module finds them per graph by
+measurement instead of hand-setting them.  It searches, with CUDA-event
+timings on a few seeded tuning sources:
+
+* the switch rule: the paper's estimate FV = |Q|*E/V, or the frontier's exact
+  edge count (``exact_fv``), which the append counter provides for free;
+* alpha (push->pull) and beta (pull->push);
+* the persistent grid size (full occupancy or half of it), the load-balance
+  knob that remains at run time -- edge tiles are balanced by construction,
+  and the per-lane / per-group widths are compile-time constants.
+
+Results do not depend on the parameters (the tests check this); only the
+time does.  The choice is cached in a JSON file keyed by a fingerprint of the
+graph (vertex and edge counts plus a hash of the log2 degree histogram).
+"""
+from __future__ import annotations
+
+import hashlib
+import itertools
+import json
+import os
+import statistics
+import time
+
+import numpy as np
+
+ALPHAS = (1e-4, 1e-3, 5e-3, 0.01, 0.05, 0.2)
+BETAS = (0.01, 0.1, 1.0)
+RULES = (0, 1)
+DEFAULT_CACHE = os.path.join(os.path.expanduser("~"), ".cache", "grx_autotune.json")
+
+
+def fingerprint(row_offsets) -> str:
+    """nv, ne and a hash of the log2-bucketed degree histogram."""
+    ro = np.asarray(row_offsets, dtype=np.int64)
+    deg = np.diff(ro)
+    buckets = np.bincount(np.floor(np.log2(deg[deg > 0])).astype(np.int64), minlength=40) \
+        if np.any(deg > 0) else np.zeros(40, dtype=np.int64)
+    h = hashlib.sha1(buckets.astype(np.int64).tobytes()).hexdigest()[:16]
+    return f"nv{ro.shape[0] - 1}_ne{int(ro[-1])}_{h}"
+
+
+def _load(path):
+    try:
+        with open(path) as f:
+            return json.load(f)
+    except Exception:
+        return {}
+
+
+def _save(path, data):
+    os.makedirs(os.path.dirname(path) or ".", exist_ok=True)
+    tmp = f"{path}.tmp{os.getpid()}"
+    with open(tmp, "w") as f:
+        json.dump(data, f, indent=1, sort_keys=True)
+    os.replace(tmp, path)
+
+
+def _time_config(grx, torch, g, sources, kw, reps):
+    """Median over sources of the per-traversal kernel time (ms)."""
+    o = grx.opts(**kw)
+    ev0 = torch.cuda.Event(enable_timing=True)
+    ev1 = torch.cuda.Event(enable_timing=True)
+    stream = torch.cuda.current_stream()
+    depth = torch.empty(g.nv, dtype=torch.int32, device=f"cuda:{g.device}")
+    ts = []
+    for s in sources:
+        grx.bfs(g, s, depth_out=depth, opts=o)           # warm
+        ev0.record(stream)
+        for _ in range(reps):
+            grx.bfs(g, s, depth_out=depth, opts=o)
+        ev1.record(stream)
+        ev1.synchronize()
+        ts.append(ev0.elapsed_time(ev1) / reps)
+    return statistics.median(ts), sum(ts)
+
+
+def tune_bfs(g, row_offsets, n_sources: int = 4, seed: int = 2, reps: int = 2,
+             cache: str | None = DEFAULT_CACHE, force: bool = False) -> dict:
+    """Search the knobs for direction-optimising BFS on a loaded graph.
+    Returns {"alpha", "beta", "exact_fv", "grid_blocks", "ms", "tried", "seconds",
+    "fingerprint", "cached"}."""
+    import torch
+
+    from . import grx, inputs
+    fp = fingerprint(row_offsets)
+    if cache and not force:
+        hit = _load(cache).get(fp)
+        if hit:
+            return dict(hit, cached=True)
+    t0 = time.time()
+    sources = [int(s) for s in inputs.pick_sources(row_offsets, n_sources, seed)]
+    grids = (0, -1)          # full occupancy, half of it
+    best = None
+    tried = 0
+    full = None
+    for rule, a, b, gsel in itertools.product(RULES, ALPHAS, BETAS, grids):
+        kw = {"exact_fv": rule, "alpha": a, "beta": b}
+        if gsel == -1:
+            if full is None:
+                continue
+            kw["grid_blocks"] = max(1, full // 2)
+        med, tot = _time_config(grx, torch, g, sources, kw, reps)
+        tried += 1
+        if best is None or tot < best[0]:
+            best = (tot, kw, med)
+        if full is None:
+            full = _occupancy_grid(grx, g)
+    tot, kw, med = best
+    grx.graph_status(g)
+    res = {"alpha": kw["alpha"], "beta": kw["beta"], "exact_fv": kw["exact_fv"],
+           "grid_blocks": kw.get("grid_blocks", 0), "ms": med, "tried": tried,
+           "seconds": time.time() - t0, "fingerprint": fp, "tuning_sources": sources}
+    if cache:
+        data = _load(cache)
+        data[fp] = res
+        _save(cache, data)
+    return dict(res, cached=False)
+
+
+def _occupancy_grid(grx, g) -> int:
+    """The persistent grid the library picks (SMs x resident blocks)."""
+    import torch
+    props = torch.cuda.get_device_properties(g.device)
+    return props.multi_processor_count * 3
+
+
+def opts_from(grx, tuned: dict, **extra):
+    """grx_opts carrying a tuning result."""
+    kw = {"alpha": tuned["alpha"], "beta": tuned["beta"], "exact_fv": tuned["exact_fv"],
+          "grid_blocks": tuned.get("grid_blocks", 0)}
+    kw.update(extra)
+    return grx.opts(**kw)

@@ -1,0 +1,40 @@
+"""Autotuner: fingerprints (host), and on the GPU a search whose choice keeps
+BFS results identical to the oracle and is cached by graph fingerprint."""
+import os
+
+import numpy as np
+import pytest
+
+import oracle
+from paper_1504_04804_gb300 import autotune, inputs
+
+
+def test_fingerprint_distinguishes_graphs_and_is_stable():
+    g1 = inputs.rmat_graph(10, 16, seed=1)
+    g2 = inputs.rmat_graph(10, 16, seed=2)
+    g3 = inputs.grid_graph(32, 32, seed=1)
+    f1 = autotune.fingerprint(g1.row_offsets)
+    assert f1 == autotune.fingerprint(g1.row_offsets.copy())
+    assert len({f1, autotune.fingerprint(g2.row_offsets), autotune.fingerprint(g3.row_offsets)}) == 3
+    assert f1.startswith(f"nv{g1.nv}_ne{g1.ne}_")
+
+
+@pytest.mark.gpu
+def test_tuned_parameters_keep_results_exact(tmp_path):
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_1504_04804_gb300 import build, grx
+    build.build()
+    g = inputs.rmat_graph(13, 16, seed=13)
+    dg = grx.load(g)
+    cache = os.path.join(tmp_path, "tune.json")
+    t = autotune.tune_bfs(dg, g.row_offsets, cache=cache)
+    assert not t["cached"] and t["tried"] >= 36
+    assert t["exact_fv"] in (0, 1) and t["alpha"] in autotune.ALPHAS and t["beta"] in autotune.BETAS
+    again = autotune.tune_bfs(dg, g.row_offsets, cache=cache)
+    assert again["cached"] and again["alpha"] == t["alpha"]
+    o = autotune.opts_from(grx, t)
+    for s in inputs.pick_sources(g.row_offsets, 4, seed=5):
+        assert np.array_equal(grx.bfs(dg, int(s), opts=o).cpu().numpy(),
+                              oracle.bfs(g.row_offsets, g.col_indices, int(s)))
