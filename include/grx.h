@@ -228,6 +228,33 @@ grx_status grx_edge_weights(int64_t nv, int64_t ne, const int64_t *row_offsets,
                             const int32_t *col_indices, uint32_t wmax, uint64_t seed,
                             uint32_t *w_out, void *stream);
 
+/* ---- continuous batching (the serving loop's device side) ---------------
+ * A batch is a resident 64-lane traversal of one graph (spec serving
+ * pattern; the paper's API runs one source at a time, Appendix A).  Queries
+ * join a free lane between level steps and leave when their own frontier is
+ * empty; each lane's result equals the single-source bfs()/sssp() result.
+ * All calls are ordered on the batch's stream. */
+#define GRX_KIND_BFS 0
+#define GRX_KIND_SSSP 1
+
+/* Open a batch of `kind` on g; its workspace (grx_batch_footprint bytes) comes
+ * from the ctx allocator.  SSSP needs weights. */
+grx_status grx_batch_open(grx_graph *g, int kind, void *stream, grx_batch **out);
+/* Synchronise the batch's stream and free it. */
+grx_status grx_batch_close(grx_batch *b);
+/* Admit a query from src into a free lane (GRX_EBUSY if all 64 are busy); it
+ * joins at the next level step.  out_dev: caller-owned device int32[nv] (BFS
+ * depth, -1 unreached) or uint32[nv] (SSSP distance, UINT32_MAX unreached)
+ * that must stay valid until the lane is reported retired. */
+grx_status grx_batch_admit(grx_batch *b, int32_t src, void *out_dev, int *lane_out);
+/* Enqueue `steps` level steps.  Does not wait. */
+grx_status grx_batch_step(grx_batch *b, int steps);
+/* Synchronise the stream; report (bit b = lane b) and free the lanes that
+ * finished since the last poll; their outputs are complete on return. */
+grx_status grx_batch_poll(grx_batch *b, uint64_t *retired_mask_out);
+/* Device bytes a batch of `kind` on g needs (for admission by free memory). */
+grx_status grx_batch_footprint(const grx_graph *g, int kind, size_t *bytes_out);
+
 #ifdef __cplusplus
 }
 #endif

@@ -80,6 +80,12 @@ SIGNATURES = [
     ("bfs_multi", _I, [_P, _P, _I, _P, _P, _P]),
     ("sssp_multi", _I, [_P, _P, _I, _P, _P, _P]),
     ("bfs_noalloc", _I, [_I64, _I64, _P, _P, ctypes.c_int32, _P, _P, _P, _P, _P]),
+    ("grx_batch_open", _I, [_P, _I, _P, _P]),
+    ("grx_batch_close", _I, [_P]),
+    ("grx_batch_admit", _I, [_P, ctypes.c_int32, _P, _P]),
+    ("grx_batch_step", _I, [_P, _I]),
+    ("grx_batch_poll", _I, [_P, _P]),
+    ("grx_batch_footprint", _I, [_P, _I, _P]),
     ("grx_rmat_edges", _I, [_I, _I64, _U64, _U64, _U64, _U64, _P, _P, _P]),
     ("grx_edge_weights", _I, [_I64, _I64, _P, _P, ctypes.c_uint32, _U64, _P, _P]),
 ]
@@ -339,6 +345,60 @@ def bfs_noalloc(row_offsets: torch.Tensor, col_indices: torch.Tensor, src: int, 
                              ctypes.byref(opts) if opts is not None else None, _stream_ptr(stream)),
            "bfs_noalloc")
     return d
+
+
+GRX_KIND_BFS, GRX_KIND_SSSP = 0, 1
+
+
+def batch_footprint(g: Graph, kind: int) -> int:
+    n = ctypes.c_size_t()
+    _check(lib().grx_batch_footprint(g.handle, int(kind), ctypes.byref(n)), "grx_batch_footprint")
+    return int(n.value)
+
+
+class Batch:
+    """A resident 64-lane traversal of one graph that queries join and leave
+    between level steps (continuous batching; see grx_batch_* in grx.h)."""
+
+    def __init__(self, g: Graph, kind: int, stream=None):
+        self.g = g
+        self.kind = int(kind)
+        self.stream = stream if stream is not None else torch.cuda.Stream(device=g.device)
+        h = ctypes.c_void_p()
+        _check(lib().grx_batch_open(g.handle, self.kind, _stream_ptr(self.stream), ctypes.byref(h)),
+               "grx_batch_open")
+        self.handle = h
+        self.outs = {}
+
+    def admit(self, src: int, out: torch.Tensor) -> int:
+        """Put a query into a free lane; raises GrxError(GRX_EBUSY) when full."""
+        lane = ctypes.c_int()
+        _check(lib().grx_batch_admit(self.handle, int(src), out.data_ptr(), ctypes.byref(lane)),
+               "grx_batch_admit")
+        self.outs[lane.value] = out
+        return lane.value
+
+    def step(self, steps: int = 1):
+        _check(lib().grx_batch_step(self.handle, int(steps)), "grx_batch_step")
+
+    def poll(self) -> int:
+        m = ctypes.c_uint64()
+        _check(lib().grx_batch_poll(self.handle, ctypes.byref(m)), "grx_batch_poll")
+        for lane in range(64):
+            if m.value >> lane & 1:
+                self.outs.pop(lane, None)
+        return int(m.value)
+
+    def close(self):
+        if self.handle:
+            lib().grx_batch_close(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
 
 
 def graph_status(g: Graph, stream=None):

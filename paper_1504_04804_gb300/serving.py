@@ -1,0 +1,259 @@
+"""Continuous-batching query server over resident graphs.
+
+Graphs stay loaded on the GPU.  Requests (a BFS or SSSP query: graph, source)
+arrive over time.  Each (graph, kind) pair has one or more 64-lane batches
+(``grx.Batch``), each on its own CUDA stream, so batches of different graphs
+run concurrently on the device.  The loop:
+
+1. admit arrived requests, first come first served, into a free lane of a
+   running batch of their graph and kind -- they join at the next level
+   boundary of a traversal already in flight -- or open a new batch when the
+   free device memory covers the batch's footprint (``grx_batch_footprint``)
+   plus the outputs it will hold; otherwise the request waits;
+2. enqueue a few level steps on every batch with work (asynchronous, one
+   stream per batch);
+3. poll every batch; a retired lane's query is complete: its latency is
+   completion minus arrival time, and its TEPS numerator (edges of the
+   reached component) is reduced on the device before the output is freed.
+
+Each query's result is exactly its single-source result (tests check alone
+vs. in the mix).  ``run_one_at_a_time`` is the baseline: the same requests
+served FIFO by single-source calls on one stream of the same GPU.
+"""
+from __future__ import annotations
+
+import time
+from dataclasses import dataclass, field
+
+import numpy as np
+
+KINDS = {"bfs": 0, "sssp": 1}
+
+
+@dataclass
+class Request:
+    rid: int
+    graph: str
+    kind: str
+    src: int
+    arrival: float                      # seconds from the start of the run
+    admitted: float = -1.0
+    done: float = -1.0
+    edges: int = 0                      # TEPS numerator (edges of the reached component)
+    result: object = None               # kept only when keep_results is set
+
+
+def make_requests(graphs: dict, n: int, rate_qps: float, seed: int = 0,
+                  kinds=("bfs", "sssp")) -> list[Request]:
+    """n requests with Poisson arrivals (rate_qps per second), graph chosen
+    uniformly, kind uniformly from kinds, source a seeded non-isolated vertex.
+    graphs: name -> (row_offsets as numpy, weighted: bool)."""
+    from . import inputs
+    rng = np.random.default_rng(seed)
+    names = sorted(graphs)
+    gaps = rng.exponential(1.0 / rate_qps, size=n) if rate_qps > 0 else np.zeros(n)
+    t = np.cumsum(gaps) - gaps[0]
+    pools = {name: inputs.pick_sources(graphs[name][0], min(4096, int(np.count_nonzero(
+        np.diff(graphs[name][0])))), seed=seed + 17 + i) for i, name in enumerate(names)}
+    reqs = []
+    for i in range(n):
+        name = names[int(rng.integers(len(names)))]
+        kind = kinds[int(rng.integers(len(kinds)))]
+        if kind == "sssp" and not graphs[name][1]:
+            kind = "bfs"
+        pool = pools[name]
+        reqs.append(Request(i, name, kind, int(pool[int(rng.integers(len(pool)))]), float(t[i])))
+    return reqs
+
+
+def plan_admission(pending: list, free_lanes: dict, free_bytes: int, footprints: dict,
+                   out_bytes: dict, open_batches: dict):
+    """Pure admission policy (host logic, testable without a GPU).
+
+    pending: requests in arrival order; free_lanes: (graph, kind) -> free lanes
+    over its open batches; free_bytes: device memory available; footprints /
+    out_bytes: (graph, kind) -> bytes of a new batch / of one query's output.
+    Returns (admit, new_batches, waiting): requests to admit now (in order),
+    (graph, kind) keys of batches to open first, and the requests that wait."""
+    lanes = dict(free_lanes)
+    budget = free_bytes
+    admit, new, waiting = [], [], []
+    for r in pending:
+        key = (r.graph, r.kind)
+        if lanes.get(key, 0) > 0 and budget >= out_bytes[key]:
+            lanes[key] -= 1
+            budget -= out_bytes[key]
+            admit.append(r)
+        elif budget >= footprints[key] + out_bytes[key]:
+            new.append(key)
+            budget -= footprints[key] + out_bytes[key]
+            lanes[key] = lanes.get(key, 0) + 63
+            admit.append(r)
+        else:
+            waiting.append(r)
+    return admit, new, waiting
+
+
+@dataclass
+class _Slot:
+    batch: object
+    key: tuple
+    lanes: dict = field(default_factory=dict)   # lane -> (request, output tensor)
+
+
+class Server:
+    def __init__(self, graphs: dict, degrees: dict, steps_per_poll: int = 2,
+                 reserve_bytes: int = 1 << 30, budget_bytes: int | None = None,
+                 keep_results: bool = False):
+        """graphs: name -> grx.Graph (loaded); degrees: name -> device int32
+        degree tensor (for the TEPS numerator).  budget_bytes caps the device
+        memory the server may use for batches (default: what is free)."""
+        import torch
+
+        from . import grx
+        self.torch, self.grx = torch, grx
+        self.graphs = graphs
+        self.degrees = degrees
+        self.steps_per_poll = steps_per_poll
+        self.reserve = reserve_bytes
+        self.budget = budget_bytes
+        self.keep = keep_results
+        self.slots: list[_Slot] = []
+        self.footprints = {}
+        self.out_bytes = {}
+        for name, g in graphs.items():
+            for kind, k in KINDS.items():
+                if kind == "sssp" and not g.weighted:
+                    continue
+                self.footprints[(name, kind)] = grx.batch_footprint(g, k)
+                self.out_bytes[(name, kind)] = 4 * g.nv
+        self.used = 0
+
+    def _free_bytes(self) -> int:
+        if self.budget is not None:
+            return self.budget - self.used
+        free, _ = self.torch.cuda.mem_get_info()
+        return free - self.reserve
+
+    def _admit(self, pending: list, now: float) -> list:
+        free_lanes = {}
+        for s in self.slots:
+            free_lanes[s.key] = free_lanes.get(s.key, 0) + 64 - len(s.lanes)
+        admit, new, waiting = plan_admission(pending, free_lanes, self._free_bytes(),
+                                             self.footprints, self.out_bytes, {})
+        for key in new:
+            g = self.graphs[key[0]]
+            b = self.grx.Batch(g, KINDS[key[1]])
+            self.slots.append(_Slot(b, key))
+            self.used += self.footprints[key]
+        for r in admit:
+            key = (r.graph, r.kind)
+            slot = next(s for s in self.slots if s.key == key and len(s.lanes) < 64)
+            g = self.graphs[r.graph]
+            with self.torch.cuda.stream(slot.batch.stream):
+                out = self.torch.empty(g.nv, dtype=self.torch.int32, device=f"cuda:{g.device}")
+            lane = slot.batch.admit(r.src, out)
+            slot.lanes[lane] = (r, out)
+            self.used += self.out_bytes[key]
+            r.admitted = now
+        return waiting
+
+    def _finish(self, slot: _Slot, mask: int, now: float, t0: float):
+        torch = self.torch
+        for lane in list(slot.lanes):
+            if not (mask >> lane & 1):
+                continue
+            r, out = slot.lanes.pop(lane)
+            deg = self.degrees[r.graph]
+            with torch.cuda.stream(slot.batch.stream):
+                if r.kind == "bfs":
+                    reached = out >= 0
+                else:
+                    reached = out != -1                  # UINT32_MAX bits read as int32 -1
+                r.edges = int((deg * reached).sum().item())
+            r.done = now
+            if self.keep:
+                r.result = out
+            self.used -= self.out_bytes[slot.key]
+
+    def run(self, requests: list[Request], realtime: bool = True) -> dict:
+        """Serve the requests (arrival times relative to the start)."""
+        torch = self.torch
+        order = sorted(requests, key=lambda r: r.arrival)
+        pending: list[Request] = []
+        nxt = 0
+        t0 = time.perf_counter()
+        inflight = 0
+        while nxt < len(order) or pending or inflight:
+            now = time.perf_counter() - t0
+            while nxt < len(order) and (order[nxt].arrival <= now or not realtime):
+                pending.append(order[nxt])
+                nxt += 1
+            if pending:
+                before = len(pending)
+                pending = self._admit(pending, now)
+                inflight += before - len(pending)
+                if pending and inflight == 0 and not self.slots_busy():
+                    raise RuntimeError("admission impossible: a batch and its outputs do not fit "
+                                       f"in the device memory budget ({self._free_bytes()} bytes free)")
+            busy = [s for s in self.slots if s.lanes]
+            for s in busy:
+                s.batch.step(self.steps_per_poll)
+            for s in busy:
+                mask = s.batch.poll()
+                if mask:
+                    done_now = time.perf_counter() - t0
+                    n_before = len(s.lanes)
+                    self._finish(s, mask, done_now, t0)
+                    inflight -= n_before - len(s.lanes)
+            if not busy and not pending and nxt < len(order) and realtime:
+                wait = order[nxt].arrival - (time.perf_counter() - t0)
+                if wait > 0:
+                    time.sleep(min(wait, 0.01))
+        torch.cuda.synchronize()
+        wall = time.perf_counter() - t0
+        return summarize(requests, wall)
+
+    def slots_busy(self) -> bool:
+        return any(s.lanes for s in self.slots)
+
+    def close(self):
+        for s in self.slots:
+            s.batch.close()
+        self.slots = []
+
+
+def summarize(requests: list[Request], wall: float) -> dict:
+    lat = np.array([r.done - r.arrival for r in requests if r.done >= 0])
+    edges = sum(r.edges for r in requests)
+    first = min(r.arrival for r in requests)
+    last = max(r.done for r in requests)
+    span = max(last - first, 1e-9)
+    return {"queries": len(requests), "p50_ms": float(np.percentile(lat, 50) * 1e3),
+            "p99_ms": float(np.percentile(lat, 99) * 1e3), "mean_ms": float(lat.mean() * 1e3),
+            "gteps": edges / span / 1e9, "span_s": span, "wall_s": wall}
+
+
+def run_one_at_a_time(graphs: dict, degrees: dict, requests: list[Request],
+                      realtime: bool = True, keep_results: bool = False) -> dict:
+    """Baseline: FIFO, one single-source traversal at a time, one stream."""
+    import torch
+
+    from . import grx
+    order = sorted(requests, key=lambda r: r.arrival)
+    t0 = time.perf_counter()
+    for r in order:
+        if realtime:
+            wait = r.arrival - (time.perf_counter() - t0)
+            if wait > 0:
+                time.sleep(wait)
+        g = graphs[r.graph]
+        r.admitted = time.perf_counter() - t0
+        out = grx.bfs(g, r.src) if r.kind == "bfs" else grx.sssp(g, r.src)
+        reached = out >= 0 if r.kind == "bfs" else out != -1
+        r.edges = int((degrees[r.graph] * reached).sum().item())
+        r.done = time.perf_counter() - t0
+        if keep_results:
+            r.result = out
+    torch.cuda.synchronize()
+    return summarize(requests, time.perf_counter() - t0)

@@ -1,0 +1,140 @@
+"""Continuous batching: the admission policy (host logic) and, on the GPU,
+that every query's result is the same alone and in the mix -- lanes joining
+a traversal already in flight, several graphs and both kinds at once."""
+import numpy as np
+import pytest
+
+import oracle
+from paper_1504_04804_gb300 import inputs, serving
+
+
+def _req(rid, graph, kind="bfs"):
+    return serving.Request(rid, graph, kind, 0, 0.0)
+
+
+def test_plan_admission_lanes_and_memory():
+    fp = {("a", "bfs"): 1000, ("b", "bfs"): 5000}
+    ob = {("a", "bfs"): 10, ("b", "bfs"): 10}
+    pend = [_req(0, "a"), _req(1, "b"), _req(2, "a")]
+    # a has one free lane, b has none and no room for a new batch
+    admit, new, wait = serving.plan_admission(pend, {("a", "bfs"): 1}, 2000, fp, ob, {})
+    assert [r.rid for r in admit] == [0, 2] and new == [("a", "bfs")] and [r.rid for r in wait] == [1]
+    # plenty of memory: one new batch per key, lanes reused afterwards
+    admit, new, wait = serving.plan_admission(pend, {}, 10**9, fp, ob, {})
+    assert [r.rid for r in admit] == [0, 1, 2] and sorted(new) == [("a", "bfs"), ("b", "bfs")]
+    assert wait == []
+    # no memory at all: nothing is admitted
+    admit, new, wait = serving.plan_admission(pend, {}, 5, fp, ob, {})
+    assert admit == [] and new == [] and len(wait) == 3
+
+
+def test_make_requests_poisson_and_seeded():
+    g = inputs.rmat_graph(10, 8, seed=1)
+    graphs = {"g1": (g.row_offsets, True), "g2": (g.row_offsets, False)}
+    r1 = serving.make_requests(graphs, 500, rate_qps=1000.0, seed=3)
+    r2 = serving.make_requests(graphs, 500, rate_qps=1000.0, seed=3)
+    assert [(r.graph, r.kind, r.src, r.arrival) for r in r1] == [(r.graph, r.kind, r.src, r.arrival) for r in r2]
+    gaps = np.diff([r.arrival for r in r1])
+    assert abs(gaps.mean() - 1e-3) < 2.5e-4                     # exponential, mean 1/rate
+    assert all(r.kind == "bfs" for r in r1 if r.graph == "g2")  # unweighted: BFS only
+    assert np.all(np.diff(g.row_offsets)[[r.src for r in r1]] > 0)
+
+
+@pytest.fixture(scope="module")
+def gpu():
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_1504_04804_gb300 import build, grx
+    build.build()
+    return torch, grx
+
+
+def _graphs():
+    return {
+        "r11": inputs.rmat_graph(11, 16, seed=11, wmax=64, weight_seed=111),
+        "r12": inputs.rmat_graph(12, 8, seed=12, wmax=64, weight_seed=112),
+        "grid": inputs.grid_graph(40, 30, p_del=0.1, seed=40, wmax=1000, weight_seed=4),
+    }
+
+
+@pytest.mark.gpu
+def test_batch_lanes_joining_mid_traversal(gpu):
+    torch, grx = gpu
+    g = _graphs()["grid"]
+    dg = grx.load(g)
+    for kind in (grx.GRX_KIND_BFS, grx.GRX_KIND_SSSP):
+        b = grx.Batch(dg, kind)
+        srcs = [int(s) for s in inputs.pick_sources(g.row_offsets, 5, seed=kind + 3)]
+        outs, done = {}, 0
+        for i, s in enumerate(srcs):                   # one new lane every 7 levels
+            out = torch.empty(g.nv, dtype=torch.int32, device="cuda")
+            lane = b.admit(s, out)
+            outs[lane] = (s, out)
+            b.step(7)
+            done |= b.poll()
+        for _ in range(10000):
+            if done == sum(1 << l for l in outs):
+                break
+            b.step(4)
+            done |= b.poll()
+        assert done == sum(1 << l for l in outs)
+        for lane, (s, out) in outs.items():
+            if kind == grx.GRX_KIND_BFS:
+                assert np.array_equal(out.cpu().numpy(), oracle.bfs(g.row_offsets, g.col_indices, s))
+            else:
+                assert np.array_equal(out.cpu().numpy().view(np.uint32),
+                                      oracle.sssp(g.row_offsets, g.col_indices, g.weights, s))
+        # the freed lanes serve new queries correctly
+        s = srcs[0]
+        out = torch.empty(g.nv, dtype=torch.int32, device="cuda")
+        b.admit(s, out)
+        while not b.poll():
+            b.step(8)
+        want = (oracle.bfs(g.row_offsets, g.col_indices, s) if kind == grx.GRX_KIND_BFS
+                else oracle.sssp(g.row_offsets, g.col_indices, g.weights, s).view(np.int32))
+        assert np.array_equal(out.cpu().numpy(), want)
+        b.close()
+
+
+@pytest.mark.gpu
+def test_server_results_same_alone_and_in_the_mix(gpu):
+    torch, grx = gpu
+    hg = _graphs()
+    graphs = {k: grx.load(v) for k, v in hg.items()}
+    degrees = {k: torch.from_numpy(np.diff(v.row_offsets).astype(np.int32)).cuda() for k, v in hg.items()}
+    reqs = serving.make_requests({k: (v.row_offsets, True) for k, v in hg.items()}, 300,
+                                 rate_qps=20000.0, seed=5)
+    srv = serving.Server(graphs, degrees, steps_per_poll=1, keep_results=True)
+    stats = srv.run(reqs)
+    srv.close()
+    assert stats["queries"] == 300 and stats["p99_ms"] >= stats["p50_ms"] > 0
+    joined_late = 0
+    for r in reqs:
+        g = hg[r.graph]
+        got = r.result.cpu().numpy()
+        if r.kind == "bfs":
+            want = oracle.bfs(g.row_offsets, g.col_indices, r.src)
+            assert np.array_equal(got, want), r
+            assert r.edges == int(np.diff(g.row_offsets)[want >= 0].sum())
+        else:
+            want = oracle.sssp(g.row_offsets, g.col_indices, g.weights, r.src)
+            assert np.array_equal(got.view(np.uint32), want), r
+        joined_late += r.admitted > 0
+    assert joined_late > 0
+    # a sample of queries run alone through the single-source entry points
+    for r in reqs[:20]:
+        alone = grx.bfs(graphs[r.graph], r.src) if r.kind == "bfs" else grx.sssp(graphs[r.graph], r.src)
+        assert np.array_equal(alone.cpu().numpy(), r.result.cpu().numpy())
+
+
+@pytest.mark.gpu
+def test_server_rejects_when_nothing_fits(gpu):
+    torch, grx = gpu
+    g = inputs.rmat_graph(10, 8, seed=2)
+    graphs = {"g": grx.load(g)}
+    degrees = {"g": torch.from_numpy(np.diff(g.row_offsets).astype(np.int32)).cuda()}
+    reqs = serving.make_requests({"g": (g.row_offsets, False)}, 3, rate_qps=0, seed=1)
+    srv = serving.Server(graphs, degrees, budget_bytes=1024)
+    with pytest.raises(RuntimeError, match="admission impossible"):
+        srv.run(reqs, realtime=False)
