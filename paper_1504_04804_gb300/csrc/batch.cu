@@ -23,7 +23,7 @@ struct BatchCtl {
     unsigned long long qpack[4];      // frontier ring (count << 32 | edges), slot = level & 3
     unsigned int ucount[4];           // touched-list ring
     int L;                            // level whose frontier is the next step's input
-    int dir;                          // direction of the step in progress
+    int dir;                          // unused (directions are per lane)
     uint32_t qprev;                   // |Q_{L-1}|
     int status;
     unsigned long long active;        // admitted, not yet retired lanes
@@ -31,6 +31,9 @@ struct BatchCtl {
     unsigned long long retired;       // lanes retired since the last poll
     int32_t start[64];                // level at which each lane joined
     void *out[64];                    // per-lane result (int32 depth or uint32 distance)
+    unsigned long long push_lanes;    // lanes expanded top-down this level
+    unsigned long long pull_lanes;    // lanes searched bottom-up this level (BFS)
+    unsigned long long lane_T[2][64]; // per-lane frontier edge count, by level parity
 };
 
 struct grx_batch {
@@ -57,7 +60,7 @@ constexpr int BT_BLOCK = 256;
 constexpr int BT_WARPS = BT_BLOCK / 32;
 constexpr int BT_ITEMS = 4;
 constexpr int BT_WTILE = 32 * BT_ITEMS;
-constexpr double BT_PULL_FRACTION = 1.0 / 20.0;   // pull when frontier edges > E/20
+constexpr double BT_PULL_FRACTION = 1.0 / 32.0;   // a lane pulls when its frontier edges > E/32
 
 template <typename T>
 __device__ __forceinline__ T pk3(T a, T b, T c, int i) { return i == 0 ? a : (i == 1 ? b : c); }
@@ -87,14 +90,22 @@ struct BtWarpSmem {
     unsigned long long cm[BT_WTILE + 1];
 };
 
-// Level begin (one thread): pick the direction, reset the ring slots.
+// Level begin (one thread): a direction per lane (Sec. 6.1 applied lane by
+// lane: a lane whose own frontier holds many edges is searched bottom-up),
+// reset the ring slots.
 template <typename OffT>
 __global__ void k_bt_begin(BatchArgs<OffT> a) {
     BatchCtl *c = a.ctl;
     const int L = c->L;
-    const unsigned long long pk = c->qpack[L & 3];
-    const uint32_t T = (uint32_t)pk;
-    c->dir = (a.kind == GRX_KIND_BFS && (double)T > BT_PULL_FRACTION * (double)a.ne) ? 1 : 0;
+    unsigned long long pull = 0ull;
+    for (int b = 0; b < 64; ++b) {
+        if (a.kind == GRX_KIND_BFS && ((c->active >> b) & 1ull) &&
+            (double)c->lane_T[L & 1][b] > BT_PULL_FRACTION * (double)a.ne)
+            pull |= 1ull << b;
+        c->lane_T[(L + 1) & 1][b] = 0ull;
+    }
+    c->pull_lanes = pull;
+    c->push_lanes = c->active & ~pull;
     c->qpack[(L + 1) & 3] = 0ull;
     c->qpack[(L + 2) & 3] = 0ull;
     c->ucount[(L + 1) & 3] = 0u;
@@ -154,13 +165,13 @@ __global__ void __launch_bounds__(BT_BLOCK) k_bt_expand(BatchArgs<OffT> a) {
     __shared__ BtWarpSmem<OffT> wsm[BT_WARPS];
     __shared__ int32_t tbufs[BT_WARPS][BT_WTILE];
     BatchCtl *c = a.ctl;
-    if (c->dir != 0) return;
     const int L = c->L;
     bt_clear_prev(a, L, c->qprev);
+    if (c->push_lanes == 0ull) return;
     BtWarpSmem<OffT> &w = wsm[threadIdx.x >> 5];
     int32_t *tbuf = tbufs[threadIdx.x >> 5];
     const unsigned int lane = threadIdx.x & 31;
-    const unsigned long long lanes = c->active;
+    const unsigned long long lanes = c->push_lanes;
     const int32_t *Qv = pk3(a.Q[0], a.Q[1], a.Q[2], L % 3);
     const uint32_t *Qe = pk3(a.E[0], a.E[1], a.E[2], L % 3);
     const OffT *Qr = pk3(a.R[0], a.R[1], a.R[2], L % 3);
@@ -170,7 +181,7 @@ __global__ void __launch_bounds__(BT_BLOCK) k_bt_expand(BatchArgs<OffT> a) {
     const int64_t q = (int64_t)(pk >> 32);
     const uint64_t T = (uint32_t)pk;
     const bool sssp = a.kind == GRX_KIND_SSSP;
-    const int wtile = sssp ? 64 : BT_WTILE;
+    const int wtile = BT_WTILE;
     const uint64_t ntiles = (T + wtile - 1) / wtile;
     const uint64_t nwarps = (uint64_t)gridDim.x * BT_WARPS;
     const uint64_t gw = (uint64_t)blockIdx.x * BT_WARPS + (threadIdx.x >> 5);
@@ -195,80 +206,71 @@ __global__ void __launch_bounds__(BT_BLOCK) k_bt_expand(BatchArgs<OffT> a) {
         const uint32_t e1 = (uint32_t)min(T, e0 + wtile);
         const int n = bt_load_tile(a, Qv, Qe, Qr, cin, lanes, q, i0, e1, wtile, w);
         const uint32_t next_start = w.qe[n];
-        int nt = 0;
-        if (!sssp) {
-            // BFS: each lane a run of BT_ITEMS edges; lanes m = cur[u] & ~seen[v] into next[v]
-            const uint64_t t0 = e0 + (uint64_t)lane * BT_ITEMS;
-            int32_t v[BT_ITEMS];
-            unsigned long long m[BT_ITEMS];
+        // each lane a run of BT_ITEMS edges; per edge the lanes to OR into
+        // next[v]: BFS m & ~seen[v]; SSSP the lanes of m whose relaxation
+        // improved D[v][lane] (cost per edge = popcount of m)
+        const uint64_t t0 = e0 + (uint64_t)lane * BT_ITEMS;
+        int32_t v[BT_ITEMS], uu[BT_ITEMS];
+        uint32_t ww[BT_ITEMS];
+        unsigned long long m[BT_ITEMS];
+#pragma unroll
+        for (int k = 0; k < BT_ITEMS; ++k) {
+            v[k] = 0;
+            uu[k] = 0;
+            ww[k] = 0;
+            m[k] = 0ull;
+        }
+        if (t0 < e1) {
+            int j = upper_index_smem(w.qe, n, (uint32_t)t0);
 #pragma unroll
             for (int k = 0; k < BT_ITEMS; ++k) {
-                v[k] = 0;
-                m[k] = 0ull;
-            }
-            if (t0 < e1) {
-                int j = upper_index_smem(w.qe, n, (uint32_t)t0);
-#pragma unroll
-                for (int k = 0; k < BT_ITEMS; ++k) {
-                    const uint32_t e = (uint32_t)t0 + k;
-                    if (e < e1) {
-                        while (w.qe[j + 1] <= e) ++j;
-                        v[k] = a.col[w.rs[j] + (OffT)(e - w.qe[j])];
-                        m[k] = w.cm[j];
+                const uint32_t e = (uint32_t)t0 + k;
+                if (e < e1) {
+                    while (w.qe[j + 1] <= e) ++j;
+                    const OffT idx = w.rs[j] + (OffT)(e - w.qe[j]);
+                    v[k] = a.col[idx];
+                    m[k] = w.cm[j];
+                    if (sssp) {
+                        ww[k] = a.w[idx];
+                        uu[k] = w.u[j];
                     }
-                }
-            }
-            uint32_t tm = 0;
-#pragma unroll
-            for (int k = 0; k < BT_ITEMS; ++k) {
-                const unsigned long long mk = m[k] ? (m[k] & ~a.seen[v[k]]) : 0ull;
-                if (mk && atomicOr(a.next + v[k], mk) == 0ull) tm |= 1u << k;
-            }
-            const uint32_t cnt = __popc(tm);
-            uint32_t incl = cnt;
-#pragma unroll
-            for (int o = 1; o < 32; o <<= 1) {
-                const uint32_t y = __shfl_up_sync(GRX_FULL_MASK, incl, o);
-                if (lane >= (unsigned)o) incl += y;
-            }
-            uint32_t p = incl - cnt;
-#pragma unroll
-            for (int k = 0; k < BT_ITEMS; ++k)
-                if (tm >> k & 1u) tbuf[p++] = v[k];
-            nt = (int)__shfl_sync(GRX_FULL_MASK, incl, 31);
-        } else {
-            // SSSP: a warp relaxes one edge for 32 lanes at a time (two halves for 64)
-            int j = 0;
-            for (uint32_t e = (uint32_t)e0; e < e1; ++e) {
-                while (w.qe[j + 1] <= e) ++j;
-                const OffT idx = w.rs[j] + (OffT)(e - w.qe[j]);
-                const int32_t vv = a.col[idx];
-                const uint32_t ww = a.w[idx];
-                const int32_t uu = w.u[j];
-                const unsigned long long mm = w.cm[j];
-                unsigned long long imp = 0ull;
-                for (int h = 0; h < 2; ++h) {
-                    const int b = (int)lane + 32 * h;
-                    bool improved = false;
-                    if ((mm >> b) & 1ull) {
-                        const uint64_t nd = (uint64_t)a.D[(int64_t)uu * 64 + b] + ww;
-                        if (nd >= 0xffffffffull) {
-                            atomicCAS(&c->status, 0, GRX_ERANGE);
-                        } else if ((uint32_t)nd < a.D[(int64_t)vv * 64 + b]) {
-                            improved = (uint32_t)nd < atomicMin(a.D + (int64_t)vv * 64 + b, (uint32_t)nd);
-                        }
-                    }
-                    imp |= (unsigned long long)__ballot_sync(GRX_FULL_MASK, improved) << (32 * h);
-                }
-                bool first = false;
-                if (lane == 0 && imp) first = atomicOr(a.next + vv, imp) == 0ull;
-                first = __shfl_sync(GRX_FULL_MASK, first, 0);
-                if (first) {
-                    if (lane == 0) tbuf[nt] = vv;
-                    ++nt;
                 }
             }
         }
+        uint32_t tm = 0;
+#pragma unroll
+        for (int k = 0; k < BT_ITEMS; ++k) {
+            unsigned long long mk = 0ull;
+            if (m[k] && !sssp) {
+                mk = m[k] & ~a.seen[v[k]];
+            } else if (m[k]) {
+                unsigned long long bits = m[k];
+                while (bits) {
+                    const int bl = __ffsll((long long)bits) - 1;
+                    bits &= bits - 1;
+                    const uint64_t nd = (uint64_t)a.D[(int64_t)uu[k] * 64 + bl] + ww[k];
+                    if (nd >= 0xffffffffull) {
+                        atomicCAS(&c->status, 0, GRX_ERANGE);
+                    } else if ((uint32_t)nd < a.D[(int64_t)v[k] * 64 + bl] &&
+                               (uint32_t)nd < atomicMin(a.D + (int64_t)v[k] * 64 + bl, (uint32_t)nd)) {
+                        mk |= 1ull << bl;
+                    }
+                }
+            }
+            if (mk && atomicOr(a.next + v[k], mk) == 0ull) tm |= 1u << k;
+        }
+        const uint32_t cnt = __popc(tm);
+        uint32_t incl = cnt;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const uint32_t y = __shfl_up_sync(GRX_FULL_MASK, incl, o);
+            if (lane >= (unsigned)o) incl += y;
+        }
+        uint32_t p = incl - cnt;
+#pragma unroll
+        for (int k = 0; k < BT_ITEMS; ++k)
+            if (tm >> k & 1u) tbuf[p++] = v[k];
+        const int nt = (int)__shfl_sync(GRX_FULL_MASK, incl, 31);
         __syncwarp();
         unsigned int base = 0;
         if (lane == 0 && nt) base = atomicAdd(tctr, (unsigned)nt);
@@ -291,13 +293,35 @@ __device__ __forceinline__ void bt_label(BatchCtl *c, int32_t v, unsigned long l
     }
 }
 
-// Touched vertices -> their new lanes, the next frontier and the alive mask.
+// Per-block per-lane frontier edge counts, flushed to lane_T of level L+1.
+struct LaneT {
+    unsigned long long t[64];
+};
+
+__device__ __forceinline__ void lane_t_add(LaneT &s, unsigned long long lanes, uint32_t deg) {
+    while (lanes) {
+        const int b = __ffsll((long long)lanes) - 1;
+        lanes &= lanes - 1;
+        atomicAdd(&s.t[b], (unsigned long long)deg);
+    }
+}
+
+__device__ __forceinline__ void lane_t_flush(LaneT &s, BatchCtl *c, int L) {
+    __syncthreads();
+    if (threadIdx.x < 64 && s.t[threadIdx.x]) atomicAdd(&c->lane_T[(L + 1) & 1][threadIdx.x], s.t[threadIdx.x]);
+}
+
+// Touched vertices -> their new push lanes, the next frontier, the alive mask.
+// Runs after the pull kernel: a vertex the pull already put in the frontier
+// only gains lanes (no second append).
 template <typename OffT>
 __global__ void __launch_bounds__(BT_BLOCK) k_bt_finalize(BatchArgs<OffT> a) {
+    __shared__ LaneT sT;
     BatchCtl *c = a.ctl;
-    if (c->dir != 0) return;
     const int L = c->L;
-    const unsigned long long lanes = c->active;
+    if (threadIdx.x < 64) sT.t[threadIdx.x] = 0ull;
+    __syncthreads();
+    const unsigned long long lanes = c->push_lanes;
     const bool bfsk = a.kind == GRX_KIND_BFS;
     unsigned long long *cout = pk3(a.cur[0], a.cur[1], a.cur[2], (L + 1) % 3);
     int32_t *Qv_out = pk3(a.Q[0], a.Q[1], a.Q[2], (L + 1) % 3);
@@ -326,12 +350,14 @@ __global__ void __launch_bounds__(BT_BLOCK) k_bt_finalize(BatchArgs<OffT> a) {
                 }
             }
             if (nw) {
-                cout[v[0]] = nw;
+                const unsigned long long before = cout[v[0]];
+                cout[v[0]] = before | nw;
                 rb[0] = a.ro[v[0]];
                 deg[0] = (uint32_t)(a.ro[v[0] + 1] - rb[0]);
                 if (deg[0]) {
-                    app = 1;
                     alive |= nw;
+                    lane_t_add(sT, nw, deg[0]);
+                    if (before == 0ull) app = 1;
                 }
             }
         }
@@ -339,16 +365,20 @@ __global__ void __launch_bounds__(BT_BLOCK) k_bt_finalize(BatchArgs<OffT> a) {
     }
     for (int o = 16; o > 0; o >>= 1) alive |= __shfl_xor_sync(GRX_FULL_MASK, alive, o);
     if ((threadIdx.x & 31) == 0 && alive) atomicOr(&c->alive, alive);
+    lane_t_flush(sT, c, L);
 }
 
-// BFS pull level: each vertex missing an active lane ORs its neighbours' cur masks.
+// BFS pull for the pull lanes: each vertex missing one of them ORs its
+// neighbours' cur masks, stopping once all its missing pull lanes are found.
 template <typename OffT>
 __global__ void __launch_bounds__(BT_BLOCK) k_bt_pull(BatchArgs<OffT> a) {
+    __shared__ LaneT sT;
     BatchCtl *c = a.ctl;
-    if (c->dir != 1) return;
+    const unsigned long long lanes = c->pull_lanes;
+    if (lanes == 0ull) return;
     const int L = c->L;
-    bt_clear_prev(a, L, c->qprev);
-    const unsigned long long lanes = c->active;
+    if (threadIdx.x < 64) sT.t[threadIdx.x] = 0ull;
+    __syncthreads();
     const unsigned long long *cin = pk3(a.cur[0], a.cur[1], a.cur[2], L % 3);
     unsigned long long *cout = pk3(a.cur[0], a.cur[1], a.cur[2], (L + 1) % 3);
     int32_t *Qv_out = pk3(a.Q[0], a.Q[1], a.Q[2], (L + 1) % 3);
@@ -377,6 +407,7 @@ __global__ void __launch_bounds__(BT_BLOCK) k_bt_pull(BatchArgs<OffT> a) {
                     deg[0] = (uint32_t)(e - b);
                     app = 1;
                     alive |= acc;
+                    lane_t_add(sT, acc, deg[0]);
                 }
             }
         }
@@ -384,6 +415,7 @@ __global__ void __launch_bounds__(BT_BLOCK) k_bt_pull(BatchArgs<OffT> a) {
     }
     for (int o = 16; o > 0; o >>= 1) alive |= __shfl_xor_sync(GRX_FULL_MASK, alive, o);
     if ((threadIdx.x & 31) == 0 && alive) atomicOr(&c->alive, alive);
+    lane_t_flush(sT, c, L);
 }
 
 // Level end (one thread): lanes absent from the new frontier retire.
@@ -430,6 +462,7 @@ __global__ void k_bt_admit(BatchArgs<OffT> a, int lane, int32_t src, void *out) 
             }
             c->start[lane] = L;
             c->out[lane] = out;
+            c->lane_T[L & 1][lane] = deg;
             c->active |= bit;
         }
     }

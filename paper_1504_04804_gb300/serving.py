@@ -99,6 +99,7 @@ class _Slot:
     batch: object
     key: tuple
     lanes: dict = field(default_factory=dict)   # lane -> (request, output tensor)
+    ev: object = None                           # event after the last enqueued steps
 
 
 class Server:
@@ -196,16 +197,24 @@ class Server:
                 if pending and inflight == 0 and not self.slots_busy():
                     raise RuntimeError("admission impossible: a batch and its outputs do not fit "
                                        f"in the device memory budget ({self._free_bytes()} bytes free)")
-            busy = [s for s in self.slots if s.lanes]
+            busy = [s for s in self.slots if s.lanes or s.ev is not None]
             for s in busy:
-                s.batch.step(self.steps_per_poll)
-            for s in busy:
-                mask = s.batch.poll()
-                if mask:
-                    done_now = time.perf_counter() - t0
-                    n_before = len(s.lanes)
-                    self._finish(s, mask, done_now, t0)
-                    inflight -= n_before - len(s.lanes)
+                # a batch whose last steps are still running is left alone, so a
+                # slow batch never holds up the others
+                if s.ev is not None and not s.ev.query():
+                    continue
+                if s.ev is not None:
+                    mask = s.batch.poll()            # its stream is idle: returns at once
+                    s.ev = None
+                    if mask:
+                        done_now = time.perf_counter() - t0
+                        n_before = len(s.lanes)
+                        self._finish(s, mask, done_now, t0)
+                        inflight -= n_before - len(s.lanes)
+                if s.lanes:
+                    s.batch.step(self.steps_per_poll)
+                    s.ev = torch.cuda.Event()
+                    s.ev.record(s.batch.stream)
             if not busy and not pending and nxt < len(order) and realtime:
                 wait = order[nxt].arrival - (time.perf_counter() - t0)
                 if wait > 0:
