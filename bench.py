@@ -226,7 +226,7 @@ def main():
     ap.add_argument("--steps", type=int, default=10)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="grx", choices=["grx", "reference"])
-    ap.add_argument("--workload", default="rmat22", choices=list(RMAT_CONFIGS))
+    ap.add_argument("--workload", default="rmat22", choices=list(RMAT_CONFIGS) + ["grid", "overhead"])
     ap.add_argument("--alpha", type=float, default=0.01)
     ap.add_argument("--beta", type=float, default=0.1)
     ap.add_argument("--cpu-budget", type=float, default=15.0,
@@ -239,6 +239,10 @@ def main():
     args = ap.parse_args()
     if args.impl == "reference":
         return reference_arm(args)
+    if args.workload == "overhead":
+        return overhead_workload(args)
+    if args.workload == "grid":
+        return grid_workload(args)
 
     import torch
     ws, rank, local = _dist_env()
@@ -413,6 +417,92 @@ def main():
     return 0
 
 
+def _loop_times(grx, torch, g, srcs, reps=3, **kw):
+    """Median device time (ms) of one BFS per loop mode."""
+    out = {}
+    for name, mode in (("persistent", grx.GRX_LOOP_PERSISTENT), ("host_stepped", grx.GRX_LOOP_HOST),
+                       ("cuda_graph", grx.GRX_LOOP_GRAPH)):
+        o = grx.opts(loop=mode, **kw)
+        ts = []
+        for s in srcs:
+            grx.bfs(g, s, opts=o)
+            a = torch.cuda.Event(enable_timing=True)
+            b = torch.cuda.Event(enable_timing=True)
+            a.record()
+            for _ in range(reps):
+                grx.bfs(g, s, opts=o)
+            b.record()
+            b.synchronize()
+            ts.append(a.elapsed_time(b) / reps)
+        out[name] = statistics.median(ts)
+    grx.graph_status(g)
+    return out
+
+
+def overhead_workload(args):
+    """Sec. 5.2's per-iteration overhead l: one vertex and one edge per level
+    (a path graph), so the time per level is the loop's fixed cost."""
+    import torch
+    from paper_1504_04804_gb300 import build, grx, inputs
+    build.build()
+    n = 10_000
+    g = inputs.csr_from_edges(n, [(i, i + 1) for i in range(n - 1)])
+    dg = grx.load(g)
+    t = _loop_times(grx, torch, dg, [0], reps=3, direction=grx.GRX_DIR_PUSH)
+    per_level = {k: v * 1e3 / n for k, v in t.items()}
+    line = {"metric": METRIC, "value": per_level["persistent"], "unit": "us/level", "n_gpus": 1,
+            "steps": 3, "warmup": 1, "higher_is_better": False, "dtype": "int32", "data": "synthetic",
+            "config": {"workload": f"path graph, {n} vertices: one vertex and one edge per BFS level "
+                                   f"({n} levels), push-only BFS from vertex 0"},
+            "per_level_us": per_level,
+            "context": "the paper measures l = 66.8 us per iteration on 1 K40 (Sec. 5.2)"}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def grid_workload(args):
+    """High-diameter grid (road-network stand-in): BFS with the three level
+    loops and SSSP, throughput and levels per second."""
+    import torch
+    from paper_1504_04804_gb300 import build, grx, inputs
+    build.build()
+    t0 = time.time()
+    hg = inputs.grid_graph(4096, 4096, p_del=0.1, seed=4096, wmax=1000, weight_seed=4196)
+    gen_s = time.time() - t0
+    g = grx.load(hg)
+    deg = np.diff(hg.row_offsets)
+    srcs = [int(s) for s in inputs.pick_sources(hg.row_offsets, 4, SOURCE_SEED)]
+    d = grx.bfs(g, srcs[0], opts=grx.opts(collect_stats=1)).cpu().numpy()
+    levels = grx.last_stats(g)["levels"]
+    edges = int(deg[d >= 0].sum())
+    t = _loop_times(grx, torch, g, srcs[:2], reps=2)
+    ss = []
+    for s in srcs[:2]:
+        a = torch.cuda.Event(enable_timing=True)
+        b = torch.cuda.Event(enable_timing=True)
+        a.record()
+        grx.sssp(g, s)
+        b.record()
+        b.synchronize()
+        ss.append(a.elapsed_time(b))
+    grx.sssp(g, srcs[0], opts=grx.opts(collect_stats=1))
+    rounds = grx.last_stats(g)["levels"]
+    grx.graph_status(g)
+    best = min(t.values())
+    line = {"metric": METRIC, "value": edges / (t["persistent"] / 1e3) / 1e9, "unit": "GTEPS",
+            "n_gpus": 1, "steps": 2, "warmup": 1, "higher_is_better": True, "dtype": "int32",
+            "data": "synthetic",
+            "config": {"workload": "grid 4096x4096, 4-neighbour, Bernoulli(0.1) edge deletion, seed 4096, "
+                                   "weights U[1,1000]; BFS and SSSP", "nv": hg.nv, "ne_directed": hg.ne,
+                       "generation_s": gen_s},
+            "bfs_levels": levels, "bfs_ms": t,
+            "bfs_levels_per_s": {k: levels / (v / 1e3) for k, v in t.items()},
+            "sssp_ms": ss, "sssp_rounds": rounds,
+            "sssp_gteps": edges / (statistics.median(ss) / 1e3) / 1e9}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
 def serving_bench(graphs: dict, degrees: dict, host_ro: dict, n_queries: int, seed: int = 7,
                   loads=(0.5, 1.0, 2.0, 4.0, 8.0)) -> dict:
     """Mixed BFS/SSSP queries with Poisson arrivals over resident graphs.
@@ -481,6 +571,23 @@ def other_primitives(grx, g, srcs, nv, ne, off_bytes, deg_h, flush, stream, peak
     ts = timed(lambda i: grx.cc(g, label_out=lab), 3)
     grx.graph_status(g)
     out["cc"] = {"ms": ts, "gteps": ne / (statistics.median(ts) / 1e3) / 1e9}
+    # 64-lane multi-source BFS and batched SSSP (one launch each)
+    from paper_1504_04804_gb300 import inputs
+    lanes =[int(s) for s in inputs.pick_sources(np.concatenate([[0], np.cumsum(deg_h)]), 64, seed=11)]
+    dm = torch.empty(64 * nv, dtype=torch.int32, device=flush.device)
+    grx.bfs_multi(g, lanes, depth_out=dm)
+    ms_edges = int(sum(int(deg_h[row >= 0].sum()) for row in dm.view(64, nv).cpu().numpy()))
+    ts = timed(lambda i: grx.bfs_multi(g, lanes, depth_out=dm), 3)
+    out["bfs_multi_64"] = {"ms": ts, "gteps": ms_edges / (statistics.median(ts) / 1e3) / 1e9,
+                           "per_query_ms": statistics.median(ts) / 64}
+    if g.weighted:
+        dd = torch.empty(16 * nv, dtype=torch.int32, device=flush.device)
+        ts = timed(lambda i: grx.sssp_multi(g, lanes[:16], dist_out=dd), 2)
+        rows = dd.view(16, nv).cpu().numpy()
+        se = int(sum(int(deg_h[row != -1].sum()) for row in rows))
+        out["sssp_multi_16"] = {"ms": ts, "gteps": se / (statistics.median(ts) / 1e3) / 1e9,
+                                "per_query_ms": statistics.median(ts) / 16}
+    grx.graph_status(g)
     # PageRank 20 iterations
     r = torch.empty(nv, dtype=torch.float32, device=flush.device)
     ts = timed(lambda i: grx.pagerank(g, 0.85, 20, rank_out=r), 3)

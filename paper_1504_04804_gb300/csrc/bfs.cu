@@ -604,6 +604,33 @@ __global__ void __launch_bounds__(BFS_BLOCK) k_bfs_step(BfsArgs<OffT> a, int lau
     run_level<OffT, PARENT, STATS>(a, st, wsm[threadIdx.x >> 5]);
 }
 
+// CUDA-graph variant: the body of a device-evaluated WHILE node is one level
+// kernel followed by a one-thread tick that derives the next level's state
+// and sets the loop condition.  The arguments live in device memory so one
+// instantiated graph serves every call on the graph.
+template <typename OffT, bool PARENT>
+__global__ void __launch_bounds__(BFS_BLOCK) k_bfs_glevel(const BfsArgs<OffT> *ap) {
+    __shared__ LevelState s_st;
+    __shared__ WarpSmem<OffT> wsm[WARPS];
+    const BfsArgs<OffT> &a = *ap;
+    if (threadIdx.x == 0) memcpy(&s_st, (const void *)a.ctl->hstate[0], sizeof(LevelState));
+    __syncthreads();
+    const LevelState st = s_st;
+    if (st.done) return;
+    run_level<OffT, PARENT, false>(a, st, wsm[threadIdx.x >> 5]);
+}
+
+template <typename OffT>
+__global__ void k_bfs_gtick(const BfsArgs<OffT> *ap, cudaGraphConditionalHandle h) {
+    const BfsArgs<OffT> &a = *ap;
+    LevelState st;
+    memcpy(&st, (const void *)a.ctl->hstate[0], sizeof st);
+    const LevelState ns = st.done ? st : next_state(a, st, false);
+    memcpy((void *)a.ctl->hstate[0], &ns, sizeof ns);
+    if (ns.done) a.ctl->levels_run = ns.L;
+    cudaGraphSetConditional(h, ns.done ? 0u : 1u);
+}
+
 template <typename OffT>
 BfsArgs<OffT> make_args(grx_graph *g, int32_t src, int32_t *depth, int32_t *parent,
                         const grx_opts *o) {
@@ -637,10 +664,77 @@ BfsArgs<OffT> make_args(grx_graph *g, int32_t src, int32_t *depth, int32_t *pare
     return a;
 }
 
+// Build (once per graph and parent flag) the instantiated CUDA graph of the
+// level loop: WHILE(cond) { level kernel -> tick kernel }.
+template <typename OffT, bool PARENT>
+grx_status graph_exec(grx_graph *g, cudaGraphExec_t *out) {
+    cudaGraphExec_t &slot = g->bfs_gexec[PARENT ? 1 : 0];
+    if (slot) {
+        *out = slot;
+        return GRX_OK;
+    }
+    if (!g->bfs_gargs) {
+        g->bfs_gargs = grx_alloc(g, sizeof(BfsArgs<int64_t>), (cudaStream_t)g->last_stream);
+        if (!g->bfs_gargs) return grx_fail(GRX_ENOMEM, "bfs: graph-mode argument block allocation failed");
+    }
+    const BfsArgs<OffT> *ap = (const BfsArgs<OffT> *)g->bfs_gargs;
+    cudaGraph_t graph = nullptr;
+    GRX_CUDA(cudaGraphCreate(&graph, 0));
+    cudaGraphConditionalHandle h;
+    cudaError_t e = cudaGraphConditionalHandleCreate(&h, graph, 1, cudaGraphCondAssignDefault);
+    cudaGraphNodeParams cp = {};
+    cp.type = cudaGraphNodeTypeConditional;
+    cp.conditional.handle = h;
+    cp.conditional.type = cudaGraphCondTypeWhile;
+    cp.conditional.size = 1;
+    cudaGraphNode_t cnode, n1, n2;
+    if (e == cudaSuccess) e = cudaGraphAddNode(&cnode, graph, nullptr, nullptr, 0, &cp);
+    if (e == cudaSuccess) {
+        cudaGraph_t body = cp.conditional.phGraph_out[0];
+        cudaKernelNodeParams k1 = {};
+        void *a1[] = {(void *)&ap};
+        k1.func = (void *)k_bfs_glevel<OffT, PARENT>;
+        k1.gridDim = dim3(g->ctx->num_sms * 3);
+        k1.blockDim = dim3(BFS_BLOCK);
+        k1.kernelParams = a1;
+        e = cudaGraphAddKernelNode(&n1, body, nullptr, 0, &k1);
+        cudaKernelNodeParams k2 = {};
+        void *a2[] = {(void *)&ap, (void *)&h};
+        k2.func = (void *)k_bfs_gtick<OffT>;
+        k2.gridDim = dim3(1);
+        k2.blockDim = dim3(1);
+        k2.kernelParams = a2;
+        if (e == cudaSuccess) e = cudaGraphAddKernelNode(&n2, body, &n1, 1, &k2);
+    }
+    if (e == cudaSuccess) e = cudaGraphInstantiate(&slot, graph, 0);
+    cudaGraphDestroy(graph);
+    if (e != cudaSuccess) {
+        slot = nullptr;
+        return grx_cuda_fail(e, "bfs: building the level-loop CUDA graph");
+    }
+    *out = slot;
+    return GRX_OK;
+}
+
 template <typename OffT, bool PARENT, bool STATS>
 grx_status launch_typed(grx_graph *g, int32_t src, int32_t *depth, int32_t *parent,
                         const grx_opts *o, cudaStream_t s) {
     BfsArgs<OffT> a = make_args<OffT>(g, src, depth, parent, o);
+    if (o->loop == GRX_LOOP_GRAPH) {
+        if (STATS) return grx_fail(GRX_EINVAL, "bfs: collect_stats needs the persistent or host loop");
+        cudaGraphExec_t ex = nullptr;
+        grx_status st = graph_exec<OffT, PARENT>(g, &ex);
+        if (st != GRX_OK) return st;
+        // arguments of this call (copied before the call returns), then the
+        // initialisation launch and the level loop
+        GRX_CUDA(cudaMemcpyAsync(g->bfs_gargs, &a, sizeof a, cudaMemcpyHostToDevice, s));
+        if (o->ev_begin) GRX_CUDA(cudaEventRecord((cudaEvent_t)o->ev_begin, s));
+        k_bfs_step<OffT, PARENT, false><<<g->ctx->num_sms * 3, BFS_BLOCK, 0, s>>>(a, 0);
+        GRX_CUDA(cudaGetLastError());
+        GRX_CUDA(cudaGraphLaunch(ex, s));
+        if (o->ev_end) GRX_CUDA(cudaEventRecord((cudaEvent_t)o->ev_end, s));
+        return GRX_OK;
+    }
     if (o->loop == GRX_LOOP_HOST) {
         int blocks = o->grid_blocks > 0 ? o->grid_blocks : g->ctx->num_sms * 4;
         // Poll the done flag every 16 launches; a traversal has at most nv levels.

@@ -290,6 +290,11 @@ fail:
 extern "C" grx_status graph_free(grx_graph *g) {
     if (!g) return GRX_OK;
     cudaStream_t s = (cudaStream_t)g->last_stream;
+    for (int i = 0; i < 2; ++i)
+        if (g->bfs_gexec[i]) {
+            cudaStreamSynchronize(s);
+            cudaGraphExecDestroy(g->bfs_gexec[i]);
+        }
     for (int i = g->nallocs - 1; i >= 0; --i) grx_ctx_free(g->ctx, g->allocs[i].p, g->allocs[i].n, s);
     free(g);
     return GRX_OK;

@@ -97,6 +97,9 @@ struct grx_graph {
     unsigned long long *ms_cur[3], *ms_next, *ms_seen;   // [nv] each
     uint32_t *ms_dist;               // batched SSSP, vertex-major [nv][64]
     int ms_ready;
+    // CUDA-graph level loop of bfs (GRX_LOOP_GRAPH), per parent flag
+    cudaGraphExec_t bfs_gexec[2];
+    void *bfs_gargs;                 // device copy of the call's arguments
     // bookkeeping for frees
     struct Alloc { void *p; size_t n; } allocs[48];
     int nallocs;

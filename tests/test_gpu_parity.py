@@ -101,13 +101,20 @@ def test_dobfs_switches_direction(grx, loaded):
     assert st["discovered"][: len(sizes) - 1] == list(sizes[1:])
 
 
-def test_bfs_host_stepped_loop(grx, loaded):
-    for name in ("rmat10", "path", "grid64"):
+@pytest.mark.parametrize("loop", ["host", "graph"])
+def test_bfs_host_stepped_and_cuda_graph_loops(grx, loaded, loop):
+    mode = grx.GRX_LOOP_HOST if loop == "host" else grx.GRX_LOOP_GRAPH
+    for name in ("rmat10", "path", "grid64", "star", "disconnected"):
         g, dg = GRAPHS[name], loaded[name]
-        o = grx.opts(loop=grx.GRX_LOOP_HOST)
-        s = _sources(g, 1, seed=2)[0]
-        d = grx.bfs(dg, s, opts=o)
-        assert np.array_equal(d.cpu().numpy(), oracle.bfs(g.row_offsets, g.col_indices, s))
+        for direction in (0, 1, 2):
+            o = grx.opts(loop=mode, direction=direction)
+            for s in _sources(g, 2, seed=2) + [g.nv - 1]:
+                d, p = grx.bfs(dg, s, opts=o, parent=True)
+                grx.graph_status(dg)
+                want = oracle.bfs(g.row_offsets, g.col_indices, s)
+                assert np.array_equal(d.cpu().numpy(), want), (loop, name, direction, s)
+                assert oracle.check_bfs(g.row_offsets, g.col_indices, s, d.cpu().numpy(),
+                                        p.cpu().numpy()) == 0
 
 
 def test_bfs_small_grids(grx, loaded):
