@@ -200,7 +200,7 @@ grx_status bfs_noalloc(int64_t nv, int64_t ne, const int32_t *row_offsets,
                        void *stream);
 
 /* ---- per-traversal counters (instrumented runs, collect_stats = 1) ------ */
-#define GRX_MAX_LEVELS_STATS 4096
+#define GRX_MAX_LEVELS_STATS 16384
 typedef struct {
     int32_t levels;            /* levels run (frontier non-empty) */
     int32_t dir[GRX_MAX_LEVELS_STATS];          /* 0 push, 1 pull */
@@ -221,6 +221,15 @@ grx_status grx_last_stats(grx_graph *g, void *stream, grx_trav_stats *out);
  * B if r < t1, C if r < t2, else D.  u_out, v_out: device int32[m]. */
 grx_status grx_rmat_edges(int scale, int64_t m, uint64_t seed, uint64_t t0, uint64_t t1,
                           uint64_t t2, int32_t *u_out, int32_t *v_out, void *stream);
+
+/* Grid lattice (stand-in for road networks, Sec. 7): width x height vertices,
+ * vertex (x,y) = y*width + x.  Horizontal edge (x,y)-(x+1,y) has id
+ * y*(width-1)+x, vertical edge (x,y)-(x,y+1) has id height*(width-1) +
+ * y*width + x; the edge is deleted when the top 53 bits of draw(seed, id) are
+ * below t_del.  Writes u_out, v_out (device int32) and keep_out (device uint8,
+ * 1 = kept) for every one of the height*(width-1)+(height-1)*width ids. */
+grx_status grx_grid_edges(int64_t width, int64_t height, uint64_t seed, uint64_t t_del,
+                          int32_t *u_out, int32_t *v_out, uint8_t *keep_out, void *stream);
 
 /* Symmetric weights: w[e] = 1 + draw(seed, min(u,v)*nv + max(u,v)) mod wmax
  * for CSR edge e = (u, v).  row_offsets int64 device [nv+1]. */

@@ -47,7 +47,46 @@ __global__ void k_weights(int64_t nv, int64_t ne, const int64_t *ro, const int32
     }
 }
 
+// Grid lattice: horizontal edge (x,y)-(x+1,y) has id y*(w-1)+x, vertical edge
+// (x,y)-(x,y+1) has id h*(w-1) + y*w + x; the edge is deleted when the top 53
+// bits of draw(seed, id) are below t_del.  Writes (u, v) for every potential
+// edge and keep[id] = 1 for the kept ones.
+__global__ void k_grid(int64_t w, int64_t h, uint64_t seed, uint64_t t_del, int32_t *u_out,
+                       int32_t *v_out, uint8_t *keep) {
+    const int64_t nh = h * (w - 1), total = nh + (h - 1) * w;
+    for (int64_t id = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; id < total;
+         id += (int64_t)gridDim.x * blockDim.x) {
+        int64_t a, b;
+        if (id < nh) {
+            const int64_t y = id / (w - 1), x = id - y * (w - 1);
+            a = y * w + x;
+            b = a + 1;
+        } else {
+            const int64_t r = id - nh, y = r / w, x = r - y * w;
+            a = y * w + x;
+            b = a + w;
+        }
+        u_out[id] = (int32_t)a;
+        v_out[id] = (int32_t)b;
+        keep[id] = (draw(seed, (uint64_t)id) >> 11) >= t_del ? 1 : 0;
+    }
+}
+
 }  // namespace
+
+extern "C" grx_status grx_grid_edges(int64_t width, int64_t height, uint64_t seed, uint64_t t_del,
+                                     int32_t *u_out, int32_t *v_out, uint8_t *keep_out, void *stream) {
+    if (width < 1 || height < 1 || width * height >= (1ll << 31) || !u_out || !v_out || !keep_out)
+        return grx_fail(GRX_EINVAL, "grx_grid_edges: bad argument");
+    const int64_t total = height * (width - 1) + (height - 1) * width;
+    if (total == 0) return GRX_OK;
+    int64_t blocks = (total + 255) / 256;
+    if (blocks > 65536) blocks = 65536;
+    k_grid<<<(unsigned)blocks, 256, 0, (cudaStream_t)stream>>>(width, height, seed, t_del, u_out, v_out,
+                                                              keep_out);
+    GRX_CUDA(cudaGetLastError());
+    return GRX_OK;
+}
 
 extern "C" grx_status grx_rmat_edges(int scale, int64_t m, uint64_t seed, uint64_t t0, uint64_t t1,
                                      uint64_t t2, int32_t *u_out, int32_t *v_out, void *stream) {

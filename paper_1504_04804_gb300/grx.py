@@ -23,7 +23,7 @@ GRX_OK, GRX_EINVAL, GRX_ENOMEM, GRX_ECUDA, GRX_ETIMEOUT, GRX_ERANGE, GRX_EBUSY =
 GRX_HOST_PTRS, GRX_DEVICE_PTRS, GRX_VALIDATE = 0x0, 0x1, 0x2
 GRX_DIR_AUTO, GRX_DIR_PUSH, GRX_DIR_PULL = 0, 1, 2
 GRX_LOOP_PERSISTENT, GRX_LOOP_HOST, GRX_LOOP_GRAPH = 0, 1, 2
-GRX_MAX_LEVELS_STATS = 4096
+GRX_MAX_LEVELS_STATS = 16384
 _STATUS_NAMES = {0: "GRX_OK", -1: "GRX_EINVAL", -2: "GRX_ENOMEM", -3: "GRX_ECUDA",
                  -4: "GRX_ETIMEOUT", -5: "GRX_ERANGE", -6: "GRX_EBUSY"}
 
@@ -88,6 +88,7 @@ SIGNATURES = [
     ("grx_batch_footprint", _I, [_P, _I, _P]),
     ("grx_rmat_edges", _I, [_I, _I64, _U64, _U64, _U64, _U64, _P, _P, _P]),
     ("grx_edge_weights", _I, [_I64, _I64, _P, _P, ctypes.c_uint32, _U64, _P, _P]),
+    ("grx_grid_edges", _I, [_I64, _I64, _U64, _U64, _P, _P, _P, _P]),
 ]
 
 _lib = None
@@ -473,6 +474,28 @@ def build_csr_device(nv: int, u: torch.Tensor, v: torch.Tensor):
     ro = torch.zeros(nv + 1, dtype=torch.int64, device=col.device)
     torch.cumsum(counts, 0, out=ro[1:])
     return ro, col
+
+
+def grid_graph_device(width: int, height: int, p_del: float = 0.1, seed: int | None = None,
+                      wmax: int | None = None, weight_seed: int | None = None, stream=None):
+    """Grid graph generated and built on the GPU (same CSR and weights as
+    inputs.grid_graph).  Returns (row_offsets, col_indices, weights|None)."""
+    from fractions import Fraction
+    seed = width if seed is None else seed
+    total = height * (width - 1) + (height - 1) * width
+    dev = torch.cuda.current_device()
+    u = torch.empty(max(total, 1), dtype=torch.int32, device=f"cuda:{dev}")
+    v = torch.empty_like(u)
+    keep = torch.empty(max(total, 1), dtype=torch.uint8, device=f"cuda:{dev}")
+    t_del = int(Fraction(str(p_del)) * (1 << 53))
+    _check(lib().grx_grid_edges(width, height, seed & (2**64 - 1), t_del, u.data_ptr(), v.data_ptr(),
+                                keep.data_ptr(), _stream_ptr(stream)), "grx_grid_edges")
+    k = keep[:total].bool()
+    ro, col = build_csr_device(width * height, u[:total][k], v[:total][k])
+    w = None
+    if wmax is not None:
+        w = edge_weights(ro, col, wmax, 100 + seed if weight_seed is None else weight_seed)
+    return ro, col, w
 
 
 def rmat_graph_device(scale: int, edge_factor: int = 16, seed: int | None = None,

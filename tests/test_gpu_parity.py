@@ -223,6 +223,12 @@ def test_device_generators_match_host(grx):
     assert np.array_equal(ro.cpu().numpy(), g.row_offsets)
     assert np.array_equal(col.cpu().numpy(), g.col_indices)
     assert np.array_equal(grx.as_uint32(w), g.weights)
+    for wd, ht in ((64, 48), (1, 5), (7, 1), (300, 211)):
+        gg = inputs.grid_graph(wd, ht, p_del=0.1, seed=wd, wmax=1000, weight_seed=9)
+        ro, col, w = grx.grid_graph_device(wd, ht, p_del=0.1, seed=wd, wmax=1000, weight_seed=9)
+        assert np.array_equal(ro.cpu().numpy(), gg.row_offsets)
+        assert np.array_equal(col.cpu().numpy(), gg.col_indices)
+        assert np.array_equal(grx.as_uint32(w), gg.weights)
 
 
 def test_load_from_device_arrays_int64_offsets(grx):
