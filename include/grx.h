@@ -71,6 +71,7 @@ const char *grx_last_error(void);
 #define GRX_VALIDATE    0x2   /* check offsets, column range, sortedness, no
                                  self-loops, symmetry and weight symmetry on
                                  the device (synchronises `stream`) */
+#define GRX_OFFSETS64   0x4   /* store 64-bit row offsets even when ne < 2^31 */
 
 /* graph_load_csr -- Sec. 7 inputs: an undirected graph with self-loops and
  * duplicate edges removed, stored as CSR (the paper's Csr, Appendix A).
@@ -80,7 +81,8 @@ const char *grx_last_error(void);
  *   weights          ne uint32 SSSP weights (Sec. 7), or NULL
  *   flags            GRX_HOST_PTRS | GRX_DEVICE_PTRS, optionally GRX_VALIDATE
  * The library copies the arrays into memory from the ctx allocator and owns
- * them until graph_free.  Offsets are stored as int32 when ne < 2^31, else
+ * them until graph_free.  Offsets are stored as int32 when ne < 2^31 (unless
+ * GRX_OFFSETS64), else
  * int64.  Returns GRX_EINVAL for malformed input (with GRX_VALIDATE), and
  * GRX_ERANGE for nv >= 2^31 or ne >= 2^32. */
 grx_status graph_load_csr(grx_ctx *ctx, int64_t nv, int64_t ne,

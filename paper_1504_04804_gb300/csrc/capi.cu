@@ -210,7 +210,7 @@ extern "C" grx_status graph_load_csr(grx_ctx *ctx, int64_t nv, int64_t ne, const
     g->ctx = ctx;
     g->nv = (int32_t)nv;
     g->ne = ne;
-    g->off64 = ne >= (1ll << 31);
+    g->off64 = ne >= (1ll << 31) || (flags & GRX_OFFSETS64) != 0;
     g->last_stream = stream;
     g->words = ((nv + 31) / 32 + 31) / 32 * 32;
     grx_status st = GRX_OK;

@@ -20,7 +20,7 @@ _HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(_HERE, "libgrx.so")
 
 GRX_OK, GRX_EINVAL, GRX_ENOMEM, GRX_ECUDA, GRX_ETIMEOUT, GRX_ERANGE, GRX_EBUSY = 0, -1, -2, -3, -4, -5, -6
-GRX_HOST_PTRS, GRX_DEVICE_PTRS, GRX_VALIDATE = 0x0, 0x1, 0x2
+GRX_HOST_PTRS, GRX_DEVICE_PTRS, GRX_VALIDATE, GRX_OFFSETS64 = 0x0, 0x1, 0x2, 0x4
 GRX_DIR_AUTO, GRX_DIR_PUSH, GRX_DIR_PULL = 0, 1, 2
 GRX_LOOP_PERSISTENT, GRX_LOOP_HOST, GRX_LOOP_GRAPH = 0, 1, 2
 GRX_MAX_LEVELS_STATS = 16384
@@ -208,10 +208,11 @@ class Graph:
 
 
 def graph_load_csr(row_offsets, col_indices, weights=None, validate: bool = False,
-                   stream=None, name: str = "") -> Graph:
+                   stream=None, name: str = "", offsets64: bool = False) -> Graph:
     """Copy a symmetric CSR (numpy arrays or torch tensors, host or device) to
     the GPU.  row_offsets int32 or int64 [nv+1], col_indices int32 [ne],
-    weights uint32 [ne] or None."""
+    weights uint32 [ne] or None.  offsets64 keeps 64-bit offsets on the device
+    even when they would fit in 32 bits."""
     ctx = _ctx()
     ro = row_offsets
     ro64 = (ro.dtype == torch.int64) if isinstance(ro, torch.Tensor) else (np.asarray(ro).dtype == np.int64)
@@ -228,7 +229,8 @@ def graph_load_csr(row_offsets, col_indices, weights=None, validate: bool = Fals
     on_dev = ro.is_cuda
     if on_dev != col.is_cuda or (w is not None and w.is_cuda != on_dev):
         raise ValueError("row_offsets, col_indices and weights must all be on the host or all on the GPU")
-    flags = (GRX_DEVICE_PTRS if on_dev else GRX_HOST_PTRS) | (GRX_VALIDATE if validate else 0)
+    flags = (GRX_DEVICE_PTRS if on_dev else GRX_HOST_PTRS) | (GRX_VALIDATE if validate else 0) | \
+        (GRX_OFFSETS64 if offsets64 else 0)
     h = ctypes.c_void_p()
     if w is not None and ne == 0:          # weighted graph without edges: any non-NULL pointer
         w = torch.zeros(1, dtype=torch.int32, device=ro.device)
@@ -245,10 +247,10 @@ def graph_free(g: Graph):
     g.free()
 
 
-def load(graph: "_inputs.Graph", validate: bool = False, stream=None) -> Graph:
+def load(graph: "_inputs.Graph", validate: bool = False, stream=None, offsets64: bool = False) -> Graph:
     """Load an inputs.Graph (host CSR) onto the GPU."""
     return graph_load_csr(graph.row_offsets, graph.col_indices, graph.weights, validate=validate,
-                          stream=stream, name=graph.name)
+                          stream=stream, name=graph.name, offsets64=offsets64)
 
 
 def opts(**kw) -> grx_opts:

@@ -133,8 +133,11 @@ class Server:
     def _free_bytes(self) -> int:
         if self.budget is not None:
             return self.budget - self.used
-        free, _ = self.torch.cuda.mem_get_info()
-        return free - self.reserve
+        torch = self.torch
+        free, _ = torch.cuda.mem_get_info()
+        # memory torch's caching allocator holds but does not use is free too
+        cached = torch.cuda.memory_reserved() - torch.cuda.memory_allocated()
+        return free + cached - self.reserve
 
     def _admit(self, pending: list, now: float) -> list:
         free_lanes = {}

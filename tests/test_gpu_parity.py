@@ -317,3 +317,51 @@ def test_multi_source_on_the_6_vertex_union(grx):
         for b, s in enumerate(srcs):
             assert np.array_equal(d[b], oracle.bfs(u.row_offsets, u.col_indices, s))
             assert np.array_equal(dist[b], oracle.sssp(u.row_offsets, u.col_indices, u.weights, s))
+
+
+@pytest.mark.parametrize("name", ["rmat13", "grid64", "path", "disconnected"])
+def test_int64_offsets_every_primitive(grx, name):
+    """The 64-bit-offset instantiation of every kernel (used when ne >= 2^31,
+    forced here on small graphs)."""
+    g = GRAPHS[name]
+    dg = grx.load(g, validate=True, offsets64=True)
+    srcs = _sources(g, 3, seed=8) + [g.nv - 1]
+    for s in srcs:
+        want = oracle.bfs(g.row_offsets, g.col_indices, s)
+        for mode in (0, 1, 2):
+            for loop in (grx.GRX_LOOP_PERSISTENT, grx.GRX_LOOP_HOST, grx.GRX_LOOP_GRAPH):
+                d = grx.bfs(dg, s, opts=grx.opts(direction=mode, loop=loop))
+                assert np.array_equal(d.cpu().numpy(), want), (name, s, mode, loop)
+        assert np.array_equal(grx.as_uint32(grx.sssp(dg, s)),
+                              oracle.sssp(g.row_offsets, g.col_indices, g.weights, s))
+    assert np.array_equal(grx.cc(dg).cpu().numpy(), oracle.cc(g.row_offsets, g.col_indices))
+    r = grx.pagerank(dg, 0.85, 20).cpu().numpy().astype(np.float64)
+    want = oracle.pagerank(g.row_offsets, g.col_indices, 0.85, 20)
+    assert np.max(np.abs(r - want) / want) <= PR_TOL
+    dm = grx.bfs_multi(dg, srcs).cpu().numpy()
+    dd = grx.sssp_multi(dg, srcs).cpu().numpy().view(np.uint32)
+    for b, s in enumerate(srcs):
+        assert np.array_equal(dm[b], oracle.bfs(g.row_offsets, g.col_indices, s))
+        assert np.array_equal(dd[b], oracle.sssp(g.row_offsets, g.col_indices, g.weights, s))
+    for kind in (grx.GRX_KIND_BFS, grx.GRX_KIND_SSSP):
+        b = grx.Batch(dg, kind)
+        outs = {}
+        for s in srcs:
+            out = torch.empty(g.nv, dtype=torch.int32, device="cuda")
+            outs[b.admit(s, out)] = (s, out)
+            b.step(3)
+        done = b.poll()
+        for _ in range(20000):
+            if done == sum(1 << l for l in outs):
+                break
+            b.step(8)
+            done |= b.poll()
+        for lane, (s, out) in outs.items():
+            got = out.cpu().numpy()
+            if kind == grx.GRX_KIND_BFS:
+                assert np.array_equal(got, oracle.bfs(g.row_offsets, g.col_indices, s))
+            else:
+                assert np.array_equal(got.view(np.uint32),
+                                      oracle.sssp(g.row_offsets, g.col_indices, g.weights, s))
+        b.close()
+    grx.graph_status(dg)
