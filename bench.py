@@ -392,6 +392,7 @@ def main():
     extra = {}
     if not args.no_extra:
         extra = other_primitives(grx, g, srcs, nv, ne, off_bytes, deg_h, flush, stream, peak)
+    if not args.no_extra and args.serving_queries > 0:
         # serving: this graph plus two smaller resident R-MAT graphs
         sgraphs, sdeg, sro = {f"rmat{cfg['scale']}": g}, {}, {f"rmat{cfg['scale']}": ro_h}
         for sc in (18, 20):

@@ -65,7 +65,44 @@ __global__ void k_fill_active(const uint32_t *bits, int64_t words, const uint32_
     }
 }
 
+// Row range of every all-edges tile: tile t covers edges [t*tile, (t+1)*tile)
+// and active rows [i0, i0 + n).  One thread per tile.
+__global__ void k_edge_tiles(const uint32_t *aoff, int64_t n_active, int64_t ne, int tile,
+                             int64_t ntiles, int2 *out) {
+    for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < ntiles;
+         t += (int64_t)gridDim.x * blockDim.x) {
+        const uint64_t e0 = (uint64_t)t * tile;
+        const uint64_t e1 = min((uint64_t)ne, e0 + tile);
+        const int64_t i0 = upper_index(aoff, n_active, (uint32_t)e0);
+        const int64_t i1 = upper_index(aoff, n_active, (uint32_t)(e1 - 1));
+        out[t] = make_int2((int)i0, (int)min(i1 - i0 + 1, (int64_t)tile + 1));
+    }
+}
+
 }  // namespace
+
+grx_status grx_edge_tiles(grx_graph *g, int tile, cudaStream_t s, const int2 **out) {
+    for (int i = 0; i < 2; ++i)
+        if (g->etiles[i] && g->etile_size[i] == tile) {
+            *out = g->etiles[i];
+            return GRX_OK;
+        }
+    int slot = g->etiles[0] ? 1 : 0;
+    if (g->etiles[slot]) return grx_fail(GRX_EINVAL, "edge tiles: more than two tile sizes requested");
+    const int64_t ntiles = (g->ne + tile - 1) / tile;
+    int2 *p = (int2 *)grx_alloc(g, (size_t)(ntiles > 0 ? ntiles : 1) * sizeof(int2), s);
+    if (!p) return grx_fail(GRX_ENOMEM, "edge tiles: allocation failed");
+    if (ntiles > 0) {
+        int64_t blocks = (ntiles + 255) / 256;
+        if (blocks > 65536) blocks = 65536;
+        k_edge_tiles<<<(unsigned)blocks, 256, 0, s>>>(g->aoff, g->n_active, g->ne, tile, ntiles, p);
+        GRX_CUDA(cudaGetLastError());
+    }
+    g->etiles[slot] = p;
+    g->etile_size[slot] = tile;
+    *out = p;
+    return GRX_OK;
+}
 
 grx_status grx_build_active(grx_graph *g, cudaStream_t s) {
     const int64_t nblocks = (g->words + ACT_WORDS_PER_BLOCK - 1) / ACT_WORDS_PER_BLOCK;

@@ -9,8 +9,9 @@
 //  * Jumping: every vertex follows parents to its root and stores it, so the
 //    next round's finds are one step.
 //  * The edge loop uses the active list (non-isolated vertices), whose edge
-//    prefix is the CSR offsets: tiles of equal edge count, row of each edge by
-//    binary search in shared memory, coalesced column reads.
+//    prefix is the CSR offsets: tiles of equal edge count (first row and row
+//    count of each tile cached per graph), row of each edge by binary search
+//    in shared memory, coalesced column reads.
 //  * One persistent cooperative kernel; hook and jump phases are separated by
 //    bounded grid barriers.  Isolated vertices keep label = own id.
 #include "grx_internal.cuh"
@@ -27,7 +28,7 @@ struct CcArgs {
     const int32_t *col;
     const int32_t *active;
     const uint32_t *aoff;
-    int64_t n_active;
+    const int2 *tiles;
     int32_t *label;
     TravCtl *ctl;
     unsigned int *bar_flags;
@@ -37,8 +38,6 @@ struct CcArgs {
 struct CcSmem {
     uint32_t qe[CC_TILE + 1];
     int32_t u[CC_TILE + 1];
-    int64_t i0;
-    int n;
     int changed;
 };
 
@@ -58,15 +57,9 @@ __device__ void hook_phase(const CcArgs &a, int round, CcSmem &sm) {
     for (uint64_t tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
         const uint64_t e0 = tile * CC_TILE;
         const uint64_t e1 = min(T, e0 + CC_TILE);
-        if (threadIdx.x == 0) {
-            int64_t i0 = upper_index(a.aoff, a.n_active, (uint32_t)e0);
-            int64_t i1 = upper_index(a.aoff, a.n_active, (uint32_t)(e1 - 1));
-            sm.i0 = i0;
-            sm.n = (int)min(i1 - i0 + 1, (int64_t)(CC_TILE + 1));
-        }
-        __syncthreads();
-        const int64_t i0 = sm.i0;
-        const int n = sm.n;
+        const int2 tr = __ldg(a.tiles + tile);
+        const int64_t i0 = tr.x;
+        const int n = tr.y;
         for (int j = threadIdx.x; j < n; j += CC_BLOCK) {
             sm.qe[j] = __ldg(a.aoff + i0 + j);
             sm.u[j] = __ldg(a.active + i0 + j);
@@ -134,7 +127,11 @@ grx_status grx_cc_launch(grx_graph *g, int32_t *label, const grx_opts *o, cudaSt
     a.col = g->col;
     a.active = g->active;
     a.aoff = g->aoff;
-    a.n_active = g->n_active;
+    a.tiles = nullptr;
+    if (g->ne > 0) {
+        grx_status st = grx_edge_tiles(g, CC_TILE, s, &a.tiles);
+        if (st != GRX_OK) return st;
+    }
     a.label = label;
     a.ctl = g->ctl;
     a.bar_flags = g->bar_flags;

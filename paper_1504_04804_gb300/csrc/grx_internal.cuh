@@ -74,6 +74,9 @@ struct grx_graph {
     int32_t *active;
     uint32_t *aoff;
     int64_t n_active;
+    // static row ranges of all-edges tiles (CC hooking, PageRank), per tile size
+    int2 *etiles[2];
+    int etile_size[2];
     void *last_stream;
     // ---- traversal workspace (allocated on first use) ----
     int ws_ready;
@@ -101,7 +104,7 @@ struct grx_graph {
     cudaGraphExec_t bfs_gexec[2];
     void *bfs_gargs;                 // device copy of the call's arguments
     // bookkeeping for frees
-    struct Alloc { void *p; size_t n; } allocs[48];
+    struct Alloc { void *p; size_t n; } allocs[64];
     int nallocs;
 };
 
@@ -123,6 +126,9 @@ grx_status grx_cuda_fail(cudaError_t e, const char *what);
 
 // Builds g->active / g->aoff / g->n_active (synchronises s once).
 grx_status grx_build_active(grx_graph *g, cudaStream_t s);
+// Cached (first active row, row count) of every tile of `tile` consecutive
+// edges over the whole edge array.
+grx_status grx_edge_tiles(grx_graph *g, int tile, cudaStream_t s, const int2 **out);
 
 grx_status grx_msbfs_launch(grx_graph *g, const int32_t *srcs, int n, int32_t *depth,
                             const grx_opts *o, cudaStream_t s);

@@ -9,9 +9,9 @@
 // base_i follow from a scalar recurrence the host evaluates in double.
 //
 // One launch per iteration over equal tiles of the edge array (the active
-// list of non-isolated vertices has the CSR offsets as its edge prefix, so
-// the rows of a tile are found by one binary search and there are at most
-// TILE+1 of them).  A tile stages c[col[e]] for its edges in shared memory;
+// list of non-isolated vertices has the CSR offsets as its edge prefix, so a
+// tile holds at most TILE+1 rows; the first row and row count of every tile
+// are computed once per graph and cached).  A tile stages c[col[e]] for its edges in shared memory;
 // each thread sums a contiguous run of edges per row and adds its partial to
 // the row's shared accumulator.  Rows inside the tile are finished there;
 // rows that cross a tile boundary add their partial to a global accumulator
@@ -31,13 +31,11 @@ struct PrSmem {
     float acc[PR_TILE + 2];
     uint32_t qe[PR_TILE + 2];
     int32_t u[PR_TILE + 2];
-    int64_t i0;
-    int n;
 };
 
 __global__ void __launch_bounds__(PR_BLOCK) k_pr_iter(
     const int32_t *__restrict__ col, const int32_t *__restrict__ active,
-    const uint32_t *__restrict__ aoff, int64_t n_active, int64_t ne,
+    const uint32_t *__restrict__ aoff, const int2 *__restrict__ tiles, int64_t ne,
     const float *__restrict__ c_in, float *__restrict__ c_out, float *__restrict__ s_acc,
     int32_t *__restrict__ fix, float *__restrict__ rank, float base, float d) {
     __shared__ PrSmem sm;
@@ -45,16 +43,10 @@ __global__ void __launch_bounds__(PR_BLOCK) k_pr_iter(
     const uint64_t e0 = tile * PR_TILE;
     const uint64_t e1 = min((uint64_t)ne, e0 + PR_TILE);
     const int len = (int)(e1 - e0);
-    if (threadIdx.x == 0) {
-        int64_t i0 = upper_index(aoff, n_active, (uint32_t)e0);
-        int64_t i1 = upper_index(aoff, n_active, (uint32_t)(e1 - 1));
-        sm.i0 = i0;
-        sm.n = (int)min(i1 - i0 + 1, (int64_t)(PR_TILE + 1));
-        fix[tile] = -1;
-    }
-    __syncthreads();
-    const int64_t i0 = sm.i0;
-    const int n = sm.n;
+    const int2 tr = __ldg(tiles + tile);
+    const int64_t i0 = tr.x;
+    const int n = tr.y;
+    if (threadIdx.x == 0) fix[tile] = -1;
     for (int j = threadIdx.x; j <= n; j += PR_BLOCK) {   // n+1 prefixes: qe[n] = end of last row
         sm.qe[j] = __ldg(aoff + i0 + j);
         if (j < n) sm.u[j] = __ldg(active + i0 + j);
@@ -163,11 +155,16 @@ grx_status grx_pr_launch(grx_graph *g, float damping, int iters, float *rank, cu
         k_pr_init<<<init_blocks > 0 ? init_blocks : 1, 256, 0, s>>>(g->active, g->aoff, g->n_active,
                                                                   (float)(1.0 / N), g->pr_c[0]);
     const int fix_blocks = (int)((ntiles + 255) / 256 > 0 ? (ntiles + 255) / 256 : 1);
+    const int2 *tiles = nullptr;
+    if (ntiles > 0) {
+        grx_status st = grx_edge_tiles(g, PR_TILE, s, &tiles);
+        if (st != GRX_OK) return st;
+    }
     for (int i = 0; i < iters && ntiles > 0; ++i) {
         const float *c_in = g->pr_c[i & 1];
         float *c_out = g->pr_c[(i + 1) & 1];
         float *r_out = i == iters - 1 ? rank : nullptr;
-        k_pr_iter<<<(unsigned)ntiles, PR_BLOCK, 0, s>>>(g->col, g->active, g->aoff, g->n_active,
+        k_pr_iter<<<(unsigned)ntiles, PR_BLOCK, 0, s>>>(g->col, g->active, g->aoff, tiles,
                                                        g->ne, c_in, c_out, g->pr_s, g->pr_fix, r_out,
                                                        base[(size_t)i], damping);
         k_pr_fixup<<<fix_blocks, 256, 0, s>>>(g->pr_fix, ntiles, g->ro, g->off64, g->pr_s, c_out, r_out,
