@@ -2,34 +2,47 @@
 //
 // Design (one GPU, GB300):
 //  * The whole traversal, including the initialisation of the outputs and
-//    bitmaps, is one cooperative persistent kernel.  Levels are separated by a
-//    flag-based grid barrier with bounded waits, so no host round trip or
-//    launch happens per level (the per-iteration overhead l of Sec. 5.2).  A
-//    host-stepped variant (one launch per level) exists for comparison.
-//  * Work inside a level is warp-independent: no block-wide barrier, so a
+//    bitmaps, is one cooperative persistent kernel.  Levels (and the phases
+//    of a level) are separated by a flag-based grid barrier with bounded
+//    waits, so no host round trip or launch happens per level (the
+//    per-iteration overhead l of Sec. 5.2).  A host-stepped variant (one
+//    launch per phase) and a CUDA-graph variant exist for comparison.
+//  * Work inside a phase is warp-independent: no block-wide barrier, so a
 //    warp waiting on memory never holds up its neighbours.
-//  * Push (top-down): advance and filter are fused (Sec. 6.3).  A frontier
-//    slot holds the vertex, its row start and the exclusive prefix of the
-//    frontier's degrees; all three come from the append that discovered the
-//    vertex (one warp-aggregated atomic), so the next level cuts the
-//    frontier's edges into equal warp tiles with no scan pass and reads a
-//    tile's rows in one round trip.  Each warp owns a contiguous range of
-//    tiles; each lane takes a run of PUSH_ITEMS consecutive edges and keeps
-//    their loads, bitmap probes and atomics in flight together.  The visited
-//    bitmap is the filter (test, then atomicOr; lanes of a warp that aim at
-//    the same vertex send one atomic; the winner labels the vertex).
-//  * Pull (bottom-up, Sec. 6.1): each lane takes PULL_PER_LANE unvisited
-//    vertices and probes their first PULL_LIGHT neighbours against the
-//    frontier bitmap at once; the vertices with longer lists and no hit yet
-//    are scanned by groups of PULL_GROUP lanes, PULL_GROUP neighbours per step,
-//    stopping at the first hit (edge skipping).  No atomics on labels.  The
-//    unvisited set is split into newly discovered vertices (appended, with
-//    degree and row start, to the next frontier, so pull->push costs nothing)
-//    and the still-unvisited list.
+//  * Frontiers: the queue Q_L (vertex, row start, exclusive prefix of the
+//    frontier's degrees) feeds push levels; the bitmap F_L feeds pull levels.
+//    Three of each rotate (slot L % 3).
+//  * Push with a small frontier (queue push): advance and filter are fused
+//    (Sec. 6.3).  The frontier's edges are cut into equal warp tiles (the
+//    degree prefix needs no scan pass); each lane takes PUSH_ITEMS
+//    consecutive edges and keeps their loads, bitmap probes and atomics in
+//    flight together.  The visited bitmap is the filter (test, then
+//    atomicOr; the winner labels the vertex and appends it with one
+//    warp-aggregated atomic).
+//  * Push with a large frontier (bitmap push, 2 phases): the same tiles mark
+//    every unvisited target in visited and F_{L+1} with fire-and-forget
+//    atomic ORs (no returned value on the path); then warps that own 32-word
+//    chunks of F_{L+1} label the marked vertices and append them to Q_{L+1}
+//    in vertex order.  Per-edge atomics with a return value and the
+//    contended append counter leave the hot loop.
+//  * Pull (bottom-up, Sec. 6.1): warps own 32-word chunks of the bitmaps.
+//    The unvisited non-isolated vertices of a chunk are compacted in shared
+//    memory; each lane takes PULL_PER_LANE of them and probes their first
+//    PULL_LIGHT neighbours against F_L at once; the lists with no hit yet
+//    are consumed together in load-balanced warp steps, each list leaving at
+//    its first step with a hit (edge skipping).  The chunk's owner writes its
+//    visited and F_{L+1} words whole: no atomics on labels, bitmaps or
+//    queues; only one counter update per warp per level.
+//  * Bitmap words that are read-only in a phase (F_L during a pull) or only
+//    filter (visited during a push: a stale 0 costs one redundant atomic,
+//    never a wrong label) are read through L1: the words of high-degree
+//    vertices are probed by most edges of a large level.  Bits written before
+//    the last grid barrier are always seen (acquire at the barrier).
+//  * A push level after pull levels first compacts F_L into Q_L (a phase).
 //  * Direction switch (Sec. 6.1): FV = |Q|*E/V, BV = |U|*V/|P|; push->pull
 //    once when FV > BV*alpha, pull->push when FV < BV*beta.  With
-//    exact_fv = 1, FV is the frontier's exact edge count, which the append
-//    atomic already provides.  Every block evaluates the rule identically.
+//    exact_fv = 1, FV is the frontier's exact edge count, which the level's
+//    counter provides.  Every block evaluates the rule identically.
 #include <cstdio>
 #include <cstring>
 
@@ -48,26 +61,35 @@ constexpr int BFS_BLOCK = 256;
 constexpr int WARPS = BFS_BLOCK / 32;
 constexpr int PUSH_ITEMS = GRX_PUSH_ITEMS;
 constexpr int WTILE = 32 * PUSH_ITEMS;              // edges per warp tile
-constexpr int PULL_LIGHT = 2;                       // neighbours probed per vertex first
+#ifndef GRX_PULL_LIGHT
+#define GRX_PULL_LIGHT 2
+#endif
+constexpr int PULL_LIGHT = GRX_PULL_LIGHT;          // neighbours probed per vertex first (1 or 2)
 constexpr int PULL_PER_LANE = 4;
-constexpr int PULL_WCH = 32 * PULL_PER_LANE;        // candidates per warp chunk
-constexpr int PULL_GROUP = 8;                       // lanes per long list
+constexpr int PULL_WCH = 32 * PULL_PER_LANE;        // candidates per warp round
+constexpr int PULL_HITEMS = PUSH_ITEMS;             // heavy-phase edges per lane per step
+constexpr int PULL_HSTEP = 32 * PULL_HITEMS;        // heavy-phase edges per warp step
+constexpr int SC_VERTS = 32 * 32;                   // vertices of a 32-word chunk
 
 enum { DIR_PUSH = 0, DIR_PULL = 1 };
+enum { OP_QPUSH, OP_BMARK, OP_BFINAL, OP_COMPACT, OP_PULL };
 
 struct LevelState {
-    int L;            // level being expanded (frontier = vertices at depth L)
-    int dir;
-    int switched;     // push->pull has happened
-    int back;         // pull->push has happened (final)
-    int first_pull;   // pull level without an unvisited list yet: scan the bitmaps
-    int fwrite;       // this level sets F_{L+1} bits for discovered vertices
-    int fprev;        // F_L holds the frontier's bits
-    int fclear;       // this level clears F_{L-1} (word by word from Q_{L-1})
-    int done;
-    uint32_t q, T;    // |Q_L| and its edge count
-    uint32_t qprev;   // |Q_{L-1}|
-    uint32_t ucount;  // unvisited-list length (non-first pull levels)
+    int L;              // level being expanded (frontier = vertices at depth L)
+    uint8_t dir;
+    uint8_t switched;   // push->pull has happened
+    uint8_t back;       // pull->push has happened (final)
+    uint8_t done;
+    uint8_t fwrite;     // this level leaves bits in F_{L+1}
+    uint8_t fprev;      // F_L may hold bits
+    uint8_t fclear;     // F_{L-1} may hold bits: this level zeroes it
+    uint8_t qin;        // Q_L exists as a queue
+    uint8_t qprev_ok;   // Q_{L-1} exists as a queue
+    uint8_t bmp;        // push by bitmap marking + finalize phase
+    uint8_t compact;    // push whose frontier is first compacted F_L -> Q_L
+    uint8_t phase;      // phase of the level being run
+    uint32_t q, T;      // |Q_L| and its edge count
+    uint32_t nprev;     // |Q_{L-1}|
     unsigned long long vcount;   // visited vertices including Q_L
 };
 
@@ -84,7 +106,6 @@ struct BfsArgs {
     int32_t *Q[3];
     uint32_t *E[3];
     OffT *R[3];
-    int32_t *U[2];
     int32_t *depth;
     int32_t *parent;
     TravCtl *ctl;
@@ -93,6 +114,7 @@ struct BfsArgs {
     int mode;
     int exact_fv;
     float alpha, beta;
+    uint32_t bmp_min_T;           // push levels with at least this many edges mark a bitmap
     unsigned long long timeout_ns;
     int32_t src;
 };
@@ -102,14 +124,18 @@ struct PushWarpSmem {
     uint32_t qe[WTILE + 2];
     int32_t u[WTILE + 1];
     OffT rs[WTILE + 1];
+    alignas(16) uint16_t rid[WTILE];   // row of each tile position
 };
 
 template <typename OffT>
 struct PullWarpSmem {
-    int32_t slot[PULL_WCH];
-    OffT hb[PULL_WCH];
-    OffT he[PULL_WCH];
-    int32_t hpar[PULL_WCH];
+    uint16_t list[SC_VERTS];       // compacted candidates of the chunk (offsets)
+    OffT hb[PULL_WCH];             // heavy lists: next edge
+    uint32_t hl[PULL_WCH];         // heavy lists: edges left
+    uint32_t hofs[PULL_WCH + 1];   // heavy lists: prefix of the unresolved lengths
+    alignas(16) uint16_t hrid[PULL_HSTEP];   // heavy step: list of each position
+    int32_t hpar[PULL_WCH];        // heavy lists: parent found (-1: none yet)
+    uint32_t fb[32];               // found bits of the chunk's words
 };
 
 template <typename OffT>
@@ -118,75 +144,229 @@ union WarpSmem {
     PullWarpSmem<OffT> l;
 };
 
+__device__ __forceinline__ int level_phases(const LevelState &s) {
+    return s.dir == DIR_PULL ? 1 : 1 + s.compact + s.bmp;
+}
+
+__device__ __forceinline__ int level_op(const LevelState &s) {
+    if (s.dir == DIR_PULL) return OP_PULL;
+    const int p = (int)s.phase - (int)s.compact;
+    if (p < 0) return OP_COMPACT;
+    if (p == 0) return s.bmp ? OP_BMARK : OP_QPUSH;
+    return OP_BFINAL;
+}
+
+template <typename OffT>
+__device__ __forceinline__ void set_kind(const BfsArgs<OffT> &a, LevelState &s) {
+    s.compact = s.dir == DIR_PUSH && !s.qin;
+    s.bmp = s.dir == DIR_PUSH && s.T >= a.bmp_min_T;
+    // a queue push feeds F_{L+1} only while a pull may still follow
+    s.fwrite = s.dir == DIR_PULL || s.bmp || (a.mode == GRX_DIR_AUTO && !s.back);
+}
+
 template <typename OffT>
 __device__ LevelState initial_state(const BfsArgs<OffT> &a) {
     LevelState s;
+    memset(&s, 0, sizeof s);
     s.L = 0;
     s.dir = a.mode == GRX_DIR_PULL ? DIR_PULL : DIR_PUSH;
     s.switched = a.mode == GRX_DIR_PULL;
-    s.back = 0;
-    s.first_pull = a.mode == GRX_DIR_PULL;
-    s.fwrite = a.mode != GRX_DIR_PUSH;
-    s.fprev = a.mode != GRX_DIR_PUSH;
-    s.fclear = 0;
-    s.done = 0;
-    uint32_t deg = (uint32_t)(__ldg(a.ro + a.src + 1) - __ldg(a.ro + a.src));
+    s.fprev = 1;                 // F_0 = {src}
+    s.qin = 1;                   // Q_0 = {src}
+    const uint32_t deg = (uint32_t)(__ldg(a.ro + a.src + 1) - __ldg(a.ro + a.src));
     s.q = deg > 0 ? 1u : 0u;
     s.T = deg;
-    s.qprev = 0;
-    s.ucount = 0;
     s.vcount = 1;
+    set_kind(a, s);
     if (s.q == 0) s.done = 1;
     return s;
 }
 
-// State of level L+1 from the state of level L and the counters level L left.
+// State of the next phase: the same level's next phase, or level L+1 from the
+// counters level L left.
 template <typename OffT>
 __device__ LevelState next_state(const BfsArgs<OffT> &a, const LevelState &st, bool stats) {
     LevelState ns = st;
+    if ((int)st.phase + 1 < level_phases(st)) {
+        ns.phase = st.phase + 1;
+        return ns;
+    }
     ns.L = st.L + 1;
-    unsigned long long pk = ld_relaxed_u64(&a.ctl->qpack[(st.L + 1) & 3]);
+    ns.phase = 0;
+    const unsigned long long pk = ld_relaxed_u64(&a.ctl->qpack[(st.L + 1) & 3]);
     ns.q = (uint32_t)(pk >> 32);
     ns.T = (uint32_t)pk;
-    ns.qprev = st.q;
-    ns.ucount = ld_relaxed_u32(&a.ctl->ucount[(st.L + 1) & 3]);
+    ns.nprev = st.q;
     ns.vcount = st.vcount + ns.q;
     ns.fclear = st.fprev;
     ns.fprev = st.fwrite;
+    ns.qprev_ok = st.qin || st.compact;
+    ns.qin = st.dir == DIR_PUSH;
     if (stats && blockIdx.x == 0 && st.L < GRX_MAX_LEVELS_STATS) a.stats->discovered[st.L] = ns.q;
     if (ns.q == 0) {
         ns.done = 1;
         return ns;
     }
-    ns.first_pull = 0;
     if (a.mode == GRX_DIR_PUSH) {
         ns.dir = DIR_PUSH;
-        ns.fwrite = 0;
     } else if (a.mode == GRX_DIR_PULL) {
         ns.dir = DIR_PULL;
-        ns.fwrite = 1;
     } else {
         // Sec. 6.1: FV = |Q|*E/V (or the exact frontier edge count), BV = |U|*V/|P|
-        double V = (double)a.nv, E = (double)a.ne;
-        double FV = a.exact_fv ? (double)ns.T : (double)ns.q * E / V;
-        double BV = (double)(a.nv - (long long)ns.vcount) * V / (double)ns.vcount;
+        const double V = (double)a.nv, E = (double)a.ne;
+        const double FV = a.exact_fv ? (double)ns.T : (double)ns.q * E / V;
+        const double BV = (double)(a.nv - (long long)ns.vcount) * V / (double)ns.vcount;
         if (st.dir == DIR_PUSH && !st.switched && FV > BV * (double)a.alpha) {
             ns.dir = DIR_PULL;
             ns.switched = 1;
-            ns.first_pull = 1;
         } else if (st.dir == DIR_PULL && FV < BV * (double)a.beta) {
             ns.dir = DIR_PUSH;
             ns.back = 1;
         }
-        ns.fwrite = !ns.back;
     }
+    set_kind(a, ns);
     return ns;
 }
 
-template <typename OffT, bool PARENT, bool STATS>
-__device__ void push_level(const BfsArgs<OffT> &a, const LevelState &st, PushWarpSmem<OffT> &w) {
-    const int L = st.L;
+// Compacts the set bits of a 32-word bitmap chunk (lane i holds word i) into
+// list[] as chunk offsets (word * 32 + bit) in increasing order.  Returns the
+// count in every lane.
+__device__ __forceinline__ int warp_compact_bits(uint32_t bits, uint16_t *list) {
     const unsigned int lane = threadIdx.x & 31;
+    const int c = __popc(bits);
+    int x = c;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const int y = __shfl_up_sync(GRX_FULL_MASK, x, o);
+        if (lane >= (unsigned)o) x += y;
+    }
+    const int total = __shfl_sync(GRX_FULL_MASK, x, 31);
+    int pos = x - c;
+    while (bits) {
+        const int b = __ffs(bits) - 1;
+        bits &= bits - 1;
+        list[pos++] = (uint16_t)(lane * 32 + b);
+    }
+    __syncwarp();
+    return total;
+}
+
+// Row of every position of a warp tile, without per-item searches or loops
+// (branches are the scarce resource of a hot tile loop): positions start at
+// row 0; each non-empty row j > 0 that starts inside the tile writes j at its
+// start; an inclusive max-scan over the positions then gives every position
+// its row.  rid holds WTILE entries, PUSH_ITEMS consecutive ones per lane;
+// starts[0..n] are the rows' first positions (non-decreasing, starts[n] =
+// end of row n-1).  On return row[k] is the row of position
+// lane*PUSH_ITEMS + k (meaningful where the position lies inside a row).
+__device__ __forceinline__ void tile_rows(uint16_t *rid, const uint32_t *starts, uint32_t origin,
+                                          int n, int (&row)[PUSH_ITEMS]) {
+    const unsigned int lane = threadIdx.x & 31;
+    static_assert(PUSH_ITEMS == 8, "tile_rows moves 8 entries per lane as one 16-byte word");
+    reinterpret_cast<uint4 *>(rid)[lane] = make_uint4(0u, 0u, 0u, 0u);
+    __syncwarp();
+    for (int j = 1 + (int)lane; j < n; j += 32) {
+        const uint32_t p = starts[j] - origin;
+        if (p < (uint32_t)WTILE && starts[j + 1] > starts[j]) rid[p] = (uint16_t)j;
+    }
+    __syncwarp();
+    const uint4 q4 = reinterpret_cast<const uint4 *>(rid)[lane];
+    const uint32_t pk[4] = {q4.x, q4.y, q4.z, q4.w};
+    int m = 0;
+#pragma unroll
+    for (int k = 0; k < PUSH_ITEMS; ++k) {
+        m = max(m, (int)((pk[k >> 1] >> ((k & 1) * 16)) & 0xffffu));
+        row[k] = m;
+    }
+    int x = m;                                   // inclusive max-scan of the lanes' maxima
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const int y = __shfl_up_sync(GRX_FULL_MASK, x, o);
+        if (lane >= (unsigned)o) x = max(x, y);
+    }
+    int carry = __shfl_up_sync(GRX_FULL_MASK, x, 1);
+    if (lane == 0) carry = 0;
+#pragma unroll
+    for (int k = 0; k < PUSH_ITEMS; ++k) row[k] = max(row[k], carry);
+    __syncwarp();
+}
+
+// Loads warp tile `tile` of the frontier's edge sequence: the frontier
+// elements that start before the tile's end go to shared memory (i0 = the
+// element holding the tile's first edge), then every lane takes PUSH_ITEMS
+// consecutive edges: destination v[k], source u[k] (when WANT_U), valid
+// bits.  Returns the element holding the next tile's first edge.
+template <typename OffT, bool WANT_U>
+__device__ __forceinline__ int64_t push_tile(const BfsArgs<OffT> &a, const int32_t *Qv,
+                                             const uint32_t *Qe, const OffT *Qr, int64_t q,
+                                             uint64_t T, uint64_t tile, int64_t i0,
+                                             PushWarpSmem<OffT> &w, int32_t (&v)[PUSH_ITEMS],
+                                             int32_t (&u)[PUSH_ITEMS], uint32_t &valid) {
+    const unsigned int lane = threadIdx.x & 31;
+    const uint64_t e0 = tile * WTILE;
+    const uint32_t e1 = (uint32_t)min(T, e0 + WTILE);
+    // frontier elements starting before e1, 32 per round; w.qe[n] ends up
+    // holding the start of the first element past the tile
+    int n = 0;
+    for (;;) {
+        const int64_t idx = i0 + n + lane;
+        uint32_t qe = 0xffffffffu;
+        if (idx < q) qe = __ldcg(Qe + idx);
+        const bool in = idx < q && qe < e1;
+        if (n + (int)lane <= WTILE + 1) w.qe[n + lane] = qe;
+        if (in && n + (int)lane <= WTILE) {
+            if (WANT_U) w.u[n + lane] = __ldcg(Qv + idx);
+            w.rs[n + lane] = __ldcg(Qr + idx);
+        }
+        const int cnt = __popc(__ballot_sync(GRX_FULL_MASK, in));
+        n += cnt;
+        if (cnt < 32) break;
+        if (n > WTILE) {              // only possible with a malformed graph
+            if (lane == 0) grx_set_status(a.ctl, GRX_EINVAL);
+            n = WTILE;
+            break;
+        }
+    }
+    __syncwarp();
+    const uint32_t next_start = w.qe[n];
+    int row[PUSH_ITEMS];
+    tile_rows(w.rid, w.qe, (uint32_t)e0, n, row);
+    const uint32_t t0 = (uint32_t)e0 + lane * PUSH_ITEMS;
+    valid = 0;
+#pragma unroll
+    for (int k = 0; k < PUSH_ITEMS; ++k) {
+        const uint32_t e = t0 + k;
+        const int j = row[k];
+        const bool ok = e < e1;
+        v[k] = ok ? __ldg(a.col + w.rs[j] + (OffT)(e - w.qe[j])) : 0;
+        u[k] = (WANT_U && ok) ? w.u[j] : 0;
+        valid |= (ok ? 1u : 0u) << k;
+    }
+    __syncwarp();
+    // the element holding e1 starts the next tile
+    return (next_start == e1) ? i0 + n : i0 + n - 1;
+}
+
+// Lanes aiming at the same vertex: only the lowest one keeps its bit.
+__device__ __forceinline__ uint32_t dedup_items(const int32_t (&v)[PUSH_ITEMS], uint32_t cand) {
+#if GRX_PUSH_DEDUP
+    uint32_t out = 0;
+#pragma unroll
+    for (int k = 0; k < PUSH_ITEMS; ++k) {
+        const bool c = cand >> k & 1u;
+        const unsigned int same = __match_any_sync(GRX_FULL_MASK, c ? v[k] : -1 - (int)(threadIdx.x & 31));
+        if (c && (same & lanemask_lt()) == 0) out |= 1u << k;
+    }
+    return out;
+#else
+    return cand;
+#endif
+}
+
+// Queue push: claim with atomicOr on visited, label, append to Q_{L+1}.
+template <typename OffT, bool PARENT>
+__device__ void push_queue(const BfsArgs<OffT> &a, const LevelState &st, PushWarpSmem<OffT> &w) {
+    const int L = st.L;
     const int32_t *Qv = pick3(a.Q[0], a.Q[1], a.Q[2], L % 3);
     const uint32_t *Qe = pick3(a.E[0], a.E[1], a.E[2], L % 3);
     const OffT *Qr = pick3(a.R[0], a.R[1], a.R[2], L % 3);
@@ -207,71 +387,18 @@ __device__ void push_level(const BfsArgs<OffT> &a, const LevelState &st, PushWar
     if (tb0 >= tb1) return;
     int64_t i0 = warp_upper_index_cg(Qe, q, (uint32_t)(tb0 * WTILE));
     for (uint64_t tile = tb0; tile < tb1; ++tile) {
-        const uint64_t e0 = tile * WTILE;
-        const uint32_t e1 = (uint32_t)min(T, e0 + WTILE);
-        // frontier elements starting before e1, 32 per round; w.qe[n] ends up
-        // holding the start of the first element past the tile
-        int n = 0;
-        for (;;) {
-            const int64_t idx = i0 + n + lane;
-            uint32_t qe = 0xffffffffu;
-            if (idx < q) qe = __ldcg(Qe + idx);
-            const bool in = idx < q && qe < e1;
-            if (n + (int)lane <= WTILE + 1) w.qe[n + lane] = qe;
-            if (in && n + (int)lane <= WTILE) {
-                w.u[n + lane] = __ldcg(Qv + idx);
-                w.rs[n + lane] = __ldcg(Qr + idx);
-            }
-            const int cnt = __popc(__ballot_sync(GRX_FULL_MASK, in));
-            n += cnt;
-            if (cnt < 32) break;
-            if (n > WTILE) {              // only possible with a malformed graph
-                if (lane == 0) grx_set_status(a.ctl, GRX_EINVAL);
-                n = WTILE;
-                break;
-            }
-        }
-        __syncwarp();
-        const uint32_t next_start = w.qe[n];
-        // a run of PUSH_ITEMS consecutive edges per lane
-        const uint64_t t0 = e0 + (uint64_t)lane * PUSH_ITEMS;
-        int32_t v[PUSH_ITEMS];
-        int32_t par[PUSH_ITEMS];
-        uint32_t valid = 0;
-#pragma unroll
-        for (int k = 0; k < PUSH_ITEMS; ++k) {
-            v[k] = 0;
-            par[k] = 0;
-        }
-        if (t0 < e1) {
-            int j = upper_index_smem(w.qe, n, (uint32_t)t0);
-#pragma unroll
-            for (int k = 0; k < PUSH_ITEMS; ++k) {
-                const uint32_t e = (uint32_t)t0 + k;
-                if (e < e1) {
-                    while (w.qe[j + 1] <= e) ++j;
-                    v[k] = __ldg(a.col + w.rs[j] + (OffT)(e - w.qe[j]));
-                    if (PARENT) par[k] = w.u[j];
-                    valid |= 1u << k;
-                }
-            }
-        }
+        int32_t v[PUSH_ITEMS], par[PUSH_ITEMS];
+        uint32_t valid;
+        i0 = push_tile<OffT, PARENT>(a, Qv, Qe, Qr, q, T, tile, i0, w, v, par, valid);
         uint32_t wv[PUSH_ITEMS];
 #pragma unroll
-        for (int k = 0; k < PUSH_ITEMS; ++k)
-            wv[k] = (valid >> k & 1u) ? __ldcg(a.visited + (v[k] >> 5)) : 0xffffffffu;
+        for (int k = 0; k < PUSH_ITEMS; ++k)   // a filter: the atomic's old value decides
+            wv[k] = (valid >> k & 1u) ? __ldca(a.visited + (v[k] >> 5)) : 0xffffffffu;
         uint32_t cand = 0;
 #pragma unroll
-        for (int k = 0; k < PUSH_ITEMS; ++k) {
-            const bool c = !((wv[k] >> (v[k] & 31)) & 1u);
-#if GRX_PUSH_DEDUP
-            // lanes aiming at the same vertex: only the lowest one tries to claim it
-            const unsigned int same = __match_any_sync(GRX_FULL_MASK, c ? v[k] : -1 - (int)lane);
-            if (c && (same & lanemask_lt()) == 0) cand |= 1u << k;
-#else
-            if (c) cand |= 1u << k;
-#endif
-        }
+        for (int k = 0; k < PUSH_ITEMS; ++k)
+            if (!((wv[k] >> (v[k] & 31)) & 1u)) cand |= 1u << k;
+        cand = dedup_items(v, cand);
         uint32_t old[PUSH_ITEMS];
 #pragma unroll
         for (int k = 0; k < PUSH_ITEMS; ++k)
@@ -305,12 +432,124 @@ __device__ void push_level(const BfsArgs<OffT> &a, const LevelState &st, PushWar
             }
         }
         warp_append_items<PUSH_ITEMS, OffT>(v, deg, rb, app, Qv_out, Qe_out, Qr_out, ctr);
-        // the element holding e1 starts the next tile
-        i0 = (next_start == e1) ? i0 + n : i0 + n - 1;
         __syncwarp();
     }
 }
 
+// Bitmap push, phase 1: every target whose visited bit is clear gets its bit
+// in visited and in F_{L+1} (reductions: no value returned).  The visited
+// probe is a filter: a stale clear bit only repeats a reduction, and bits of
+// earlier levels are always seen (they were written before the level's
+// barrier), so F_{L+1} ends up holding exactly the vertices first reached in
+// this level.  One probe per edge is the cost that matters: each is a random
+// cache line.  With PARENT, a marking lane stores its source as the parent:
+// every writer is a valid parent, one of them remains.
+template <typename OffT, bool PARENT>
+__device__ void push_mark(const BfsArgs<OffT> &a, const LevelState &st, PushWarpSmem<OffT> &w) {
+    const int L = st.L;
+    const int32_t *Qv = pick3(a.Q[0], a.Q[1], a.Q[2], L % 3);
+    const uint32_t *Qe = pick3(a.E[0], a.E[1], a.E[2], L % 3);
+    const OffT *Qr = pick3(a.R[0], a.R[1], a.R[2], L % 3);
+    uint32_t *Fout = pick3(a.F[0], a.F[1], a.F[2], (L + 1) % 3);
+    const int64_t q = st.q;
+    const uint64_t T = st.T;
+    const uint64_t ntiles = (T + WTILE - 1) / WTILE;
+    const uint64_t nwarps = (uint64_t)gridDim.x * WARPS;
+    const uint64_t gw = (uint64_t)blockIdx.x * WARPS + (threadIdx.x >> 5);
+    const uint64_t per = (ntiles + nwarps - 1) / nwarps;
+    const uint64_t tb0 = gw * per;
+    const uint64_t tb1 = min(ntiles, tb0 + per);
+    if (tb0 >= tb1) return;
+    int64_t i0 = warp_upper_index_cg(Qe, q, (uint32_t)(tb0 * WTILE));
+    for (uint64_t tile = tb0; tile < tb1; ++tile) {
+        int32_t v[PUSH_ITEMS], par[PUSH_ITEMS];
+        uint32_t valid;
+        i0 = push_tile<OffT, PARENT>(a, Qv, Qe, Qr, q, T, tile, i0, w, v, par, valid);
+        uint32_t wv[PUSH_ITEMS];
+#pragma unroll
+        for (int k = 0; k < PUSH_ITEMS; ++k)
+            wv[k] = (valid >> k & 1u) ? __ldca(a.visited + (v[k] >> 5)) : 0xffffffffu;
+#pragma unroll
+        for (int k = 0; k < PUSH_ITEMS; ++k) {
+            if (!((wv[k] >> (v[k] & 31)) & 1u)) {
+                const uint32_t bit = 1u << (v[k] & 31);
+                if (PARENT) a.parent[v[k]] = par[k];
+                atomicOr(a.visited + (v[k] >> 5), bit);     // results unused: reductions
+                atomicOr(Fout + (v[k] >> 5), bit);
+            }
+        }
+    }
+}
+
+// Word-owning pass from a frontier bitmap to a frontier queue.  FINAL (bitmap
+// push, phase 2): B = F_{L+1} (already in visited); its vertices are
+// labelled L+1 and appended to Q_{L+1} (counter of level L).  Otherwise (compaction
+// before a push level): B = F_L, appended to Q_L through the compaction
+// counter.  Vertices without edges are labelled but not queued.
+template <typename OffT, bool FINAL>
+__device__ void bitmap_to_queue(const BfsArgs<OffT> &a, const LevelState &st, PullWarpSmem<OffT> &w) {
+    const int L = st.L;
+    const int ring = FINAL ? (L + 1) % 3 : L % 3;
+    uint32_t *B = pick3(a.F[0], a.F[1], a.F[2], ring);
+    int32_t *Qv = pick3(a.Q[0], a.Q[1], a.Q[2], ring);
+    uint32_t *Qe = pick3(a.E[0], a.E[1], a.E[2], ring);
+    OffT *Qr = pick3(a.R[0], a.R[1], a.R[2], ring);
+    unsigned long long *ctr = FINAL ? &a.ctl->qpack[(L + 1) & 3] : &a.ctl->cpack;
+    const unsigned int lane = threadIdx.x & 31;
+    const int64_t nsc = (a.words + 31) / 32;
+    const int64_t nwarps = (int64_t)gridDim.x * WARPS;
+    for (int64_t sc = (int64_t)blockIdx.x * WARPS + (threadIdx.x >> 5); sc < nsc; sc += nwarps) {
+        const int64_t wd = sc * 32 + lane;
+        const uint32_t bits = wd < a.words ? __ldcg(B + wd) : 0u;
+        if (FINAL && bits) {
+            // a frontier bitmap holds vertices with edges only (as the queue does)
+            const uint32_t nzw = __ldg(a.nz + wd);
+            if (bits & ~nzw) B[wd] = bits & nzw;
+        }
+        const int n = warp_compact_bits(bits, w.list);
+        for (int base = 0; base < n; base += PULL_WCH) {
+            int32_t v[PULL_PER_LANE];
+            OffT rb[PULL_PER_LANE], re[PULL_PER_LANE];
+            uint32_t deg[PULL_PER_LANE];
+            uint32_t app = 0;
+#pragma unroll
+            for (int k = 0; k < PULL_PER_LANE; ++k) {
+                const int i = base + k * 32 + (int)lane;
+                v[k] = i < n ? (int32_t)(sc * SC_VERTS + w.list[i]) : -1;
+                rb[k] = 0;
+                re[k] = 0;
+                if (v[k] >= 0) {
+                    rb[k] = __ldg(a.ro + v[k]);
+                    re[k] = __ldg(a.ro + v[k] + 1);
+                }
+            }
+#pragma unroll
+            for (int k = 0; k < PULL_PER_LANE; ++k) {
+                deg[k] = (uint32_t)(re[k] - rb[k]);
+                if (v[k] >= 0) {
+                    if (FINAL) a.depth[v[k]] = L + 1;
+                    if (deg[k]) app |= 1u << k;
+                }
+            }
+            warp_append_items<PULL_PER_LANE, OffT>(v, deg, rb, app, Qv, Qe, Qr, ctr);
+        }
+        __syncwarp();
+    }
+}
+
+// Pull level: the owner of each 32-word chunk finds a frontier parent for the
+// chunk's unvisited non-isolated vertices and writes the chunk's visited and
+// F_{L+1} words (and, with fclear, zeroes its F_{L-1} words).
+//  1. candidates of the chunk, PULL_WCH per round (PULL_PER_LANE per lane);
+//  2. light phase: the first PULL_LIGHT neighbours of every candidate, all in
+//     flight at once;
+//  3. heavy phase: the round's lists without a hit yet are concatenated and
+//     consumed front to back in load-balanced steps of PULL_HSTEP edges
+//     shared by the whole warp; a list leaves once any of its edges hits the
+//     frontier (any frontier neighbour is a valid parent);
+//  4. found vertices are labelled; their bits collect in the chunk's masks.
+// F_L is read-only during the level, so its probes may be served by L1 (hot
+// words of high-degree vertices are then not refetched from L2 by every warp).
 template <typename OffT, bool PARENT, bool STATS>
 __device__ void pull_level(const BfsArgs<OffT> &a, const LevelState &st, PullWarpSmem<OffT> &w,
                            unsigned long long &scanned_e, unsigned long long &scanned_v) {
@@ -318,187 +557,207 @@ __device__ void pull_level(const BfsArgs<OffT> &a, const LevelState &st, PullWar
     const unsigned int lane = threadIdx.x & 31;
     const uint32_t *Fin = pick3(a.F[0], a.F[1], a.F[2], L % 3);
     uint32_t *Fout = pick3(a.F[0], a.F[1], a.F[2], (L + 1) % 3);
-    int32_t *Qv_out = pick3(a.Q[0], a.Q[1], a.Q[2], (L + 1) % 3);
-    uint32_t *Qe_out = pick3(a.E[0], a.E[1], a.E[2], (L + 1) % 3);
-    OffT *Qr_out = pick3(a.R[0], a.R[1], a.R[2], (L + 1) % 3);
-    unsigned long long *ctr = &a.ctl->qpack[(L + 1) & 3];
-    const int32_t *Uin = (L & 1) ? a.U[1] : a.U[0];
-    int32_t *Uout = (L & 1) ? a.U[0] : a.U[1];
-    unsigned int *uctr = &a.ctl->ucount[(L + 1) & 3];
-    const bool first = st.first_pull != 0;
-    const int64_t nchunks = first ? (a.words + PULL_PER_LANE - 1) / PULL_PER_LANE
-                                  : ((int64_t)st.ucount + PULL_WCH - 1) / PULL_WCH;
+    uint32_t *Fold = pick3(a.F[0], a.F[1], a.F[2], (L + 2) % 3);
+    const int64_t nsc = (a.words + 31) / 32;
     const int64_t nwarps = (int64_t)gridDim.x * WARPS;
-    const int64_t gw = (int64_t)blockIdx.x * WARPS + (threadIdx.x >> 5);
-    for (int64_t c = gw; c < nchunks; c += nwarps) {
-        // 1. candidates: lane takes vertex k*32+lane of the chunk
-        int32_t v[PULL_PER_LANE];
-        if (first) {
-            uint32_t any = 0;
+    uint32_t nfound = 0;
+    uint32_t nedges = 0;
+    for (int64_t sc = (int64_t)blockIdx.x * WARPS + (threadIdx.x >> 5); sc < nsc; sc += nwarps) {
+        const int64_t wd = sc * 32 + lane;
+        const bool own = wd < a.words;
+        const uint32_t vis = own ? __ldcg(a.visited + wd) : 0xffffffffu;
+        const uint32_t cand = own ? (__ldg(a.nz + wd) & ~vis) : 0u;
+        if (own && st.fclear) Fold[wd] = 0u;
+        w.fb[lane] = 0u;
+        const int n = warp_compact_bits(cand, w.list);
+        for (int base = 0; base < n; base += PULL_WCH) {
+            // 1. candidates: lane takes entries base + k*32 + lane
+            int32_t v[PULL_PER_LANE];
 #pragma unroll
             for (int k = 0; k < PULL_PER_LANE; ++k) {
-                const int64_t wd = c * PULL_PER_LANE + k;
-                const uint32_t bits = wd < a.words ? (__ldg(a.nz + wd) & ~__ldcg(a.visited + wd)) : 0u;
-                any |= bits;
-                v[k] = ((bits >> lane) & 1u) ? (int32_t)(wd * 32 + lane) : -1;
+                const int i = base + k * 32 + (int)lane;
+                v[k] = i < n ? (int32_t)(sc * SC_VERTS + w.list[i]) : -1;
             }
-            if (any == 0) continue;                  // same words in every lane
-        } else {
+            // 2. light phase
+            OffT b[PULL_PER_LANE];
+            uint32_t deg[PULL_PER_LANE];
 #pragma unroll
             for (int k = 0; k < PULL_PER_LANE; ++k) {
-                const int64_t i = c * PULL_WCH + k * 32 + lane;
-                v[k] = i < (int64_t)st.ucount ? __ldcg(Uin + i) : -1;
-            }
-        }
-        // 2. light phase: the first PULL_LIGHT neighbours of every candidate, all in flight
-        OffT b[PULL_PER_LANE], e[PULL_PER_LANE];
-#pragma unroll
-        for (int k = 0; k < PULL_PER_LANE; ++k) {
-            b[k] = 0;
-            e[k] = 0;
-            if (v[k] >= 0) {
-                b[k] = __ldg(a.ro + v[k]);
-                e[k] = __ldg(a.ro + v[k] + 1);
-            }
-        }
-        int32_t u0[PULL_PER_LANE], u1[PULL_PER_LANE];
-#pragma unroll
-        for (int k = 0; k < PULL_PER_LANE; ++k) {
-            u0[k] = b[k] < e[k] ? __ldg(a.col + b[k]) : -1;
-            u1[k] = b[k] + 1 < e[k] ? __ldg(a.col + b[k] + 1) : -1;
-        }
-        uint32_t f0[PULL_PER_LANE], f1[PULL_PER_LANE];
-#pragma unroll
-        for (int k = 0; k < PULL_PER_LANE; ++k) {
-            f0[k] = u0[k] >= 0 ? __ldcg(Fin + (u0[k] >> 5)) : 0u;
-            f1[k] = u1[k] >= 0 ? __ldcg(Fin + (u1[k] >> 5)) : 0u;
-        }
-        int32_t par[PULL_PER_LANE];
-        uint32_t heavy = 0;
-#pragma unroll
-        for (int k = 0; k < PULL_PER_LANE; ++k) {
-            par[k] = -1;
-            if (u0[k] >= 0 && ((f0[k] >> (u0[k] & 31)) & 1u)) par[k] = u0[k];
-            else if (u1[k] >= 0 && ((f1[k] >> (u1[k] & 31)) & 1u)) par[k] = u1[k];
-            if (STATS && v[k] >= 0) {
-                scanned_v += 1;
-                scanned_e += (unsigned long long)min((OffT)PULL_LIGHT, e[k] - b[k]);
-            }
-            if (v[k] >= 0 && par[k] < 0 && e[k] - b[k] > PULL_LIGHT) heavy |= 1u << k;
-        }
-        // 3. heavy phase: the warp's longer lists, PULL_GROUP lanes each
-        int nh = 0;
-        int hpos[PULL_PER_LANE];
-#pragma unroll
-        for (int k = 0; k < PULL_PER_LANE; ++k) {
-            const unsigned int m = __ballot_sync(GRX_FULL_MASK, heavy >> k & 1u);
-            hpos[k] = nh + __popc(m & lanemask_lt());
-            if (heavy >> k & 1u) {
-                w.hb[hpos[k]] = b[k] + PULL_LIGHT;
-                w.he[hpos[k]] = e[k];
-            }
-            nh += __popc(m);
-        }
-        __syncwarp();
-        const int grp = (int)(lane / PULL_GROUP), gl = (int)(lane % PULL_GROUP);
-        for (int h0 = 0; h0 < nh; h0 += 32 / PULL_GROUP) {
-            const int h = h0 + grp;
-            OffT hb = 0, he = 0;
-            if (h < nh) {
-                hb = w.hb[h];
-                he = w.he[h];
-            }
-            int32_t found = -1;
-            bool done = h >= nh;
-            while (__any_sync(GRX_FULL_MASK, !done)) {
-                int32_t uu = -1;
-                bool hit = false;
-                if (!done && hb + gl < he) {
-                    uu = __ldg(a.col + hb + gl);
-                    hit = (__ldcg(Fin + (uu >> 5)) >> (uu & 31)) & 1u;
+                b[k] = 0;
+                deg[k] = 0;
+                if (v[k] >= 0) {
+                    b[k] = __ldg(a.ro + v[k]);
+                    deg[k] = (uint32_t)(__ldg(a.ro + v[k] + 1) - b[k]);
                 }
-                const unsigned int gm = (__ballot_sync(GRX_FULL_MASK, hit) >> (grp * PULL_GROUP)) &
-                                        ((1u << PULL_GROUP) - 1u);
-                const int32_t first_hit =
-                    __shfl_sync(GRX_FULL_MASK, uu, grp * PULL_GROUP + (gm ? __ffs(gm) - 1 : 0));
-                if (!done) {
-                    if (STATS && gl == 0)
-                        scanned_e += (unsigned long long)(gm ? __ffs(gm) : min((OffT)PULL_GROUP, he - hb));
-                    if (gm) {
-                        found = first_hit;
-                        done = true;
-                    } else {
-                        hb += PULL_GROUP;
-                        done = hb >= he;
+            }
+            static_assert(PULL_LIGHT == 1 || PULL_LIGHT == 2, "light phase probes 1 or 2 neighbours");
+            int32_t u0[PULL_PER_LANE], u1[PULL_PER_LANE];
+#pragma unroll
+            for (int k = 0; k < PULL_PER_LANE; ++k) {
+                u0[k] = deg[k] > 0 ? __ldg(a.col + b[k]) : -1;
+                u1[k] = (PULL_LIGHT > 1 && deg[k] > 1) ? __ldg(a.col + b[k] + 1) : -1;
+            }
+            uint32_t f0[PULL_PER_LANE], f1[PULL_PER_LANE];
+#pragma unroll
+            for (int k = 0; k < PULL_PER_LANE; ++k) {
+                f0[k] = u0[k] >= 0 ? __ldca(Fin + (u0[k] >> 5)) : 0u;
+                f1[k] = u1[k] >= 0 ? __ldca(Fin + (u1[k] >> 5)) : 0u;
+            }
+            int32_t par[PULL_PER_LANE];
+            uint32_t heavy = 0;
+#pragma unroll
+            for (int k = 0; k < PULL_PER_LANE; ++k) {
+                par[k] = -1;
+                if (u0[k] >= 0 && ((f0[k] >> (u0[k] & 31)) & 1u)) par[k] = u0[k];
+                else if (u1[k] >= 0 && ((f1[k] >> (u1[k] & 31)) & 1u)) par[k] = u1[k];
+                if (STATS && v[k] >= 0) {
+                    scanned_v += 1;
+                    scanned_e += (unsigned long long)min((uint32_t)PULL_LIGHT, deg[k]);
+                }
+                if (v[k] >= 0 && par[k] < 0 && deg[k] > PULL_LIGHT) heavy |= 1u << k;
+            }
+            // 3. heavy phase
+            int nh = 0;
+            int hpos[PULL_PER_LANE];
+#pragma unroll
+            for (int k = 0; k < PULL_PER_LANE; ++k) {
+                const unsigned int m = __ballot_sync(GRX_FULL_MASK, heavy >> k & 1u);
+                hpos[k] = nh + __popc(m & lanemask_lt());
+                if (heavy >> k & 1u) {
+                    w.hb[hpos[k]] = b[k] + PULL_LIGHT;
+                    w.hl[hpos[k]] = deg[k] - PULL_LIGHT;
+                    w.hpar[hpos[k]] = -1;
+                }
+                nh += __popc(m);
+            }
+            __syncwarp();
+            while (nh > 0) {
+                // exclusive prefix of the unresolved lengths; lane owns entries lane*PULL_PER_LANE + r
+                uint32_t ln[PULL_PER_LANE], lsum = 0;
+#pragma unroll
+                for (int r = 0; r < PULL_PER_LANE; ++r) {
+                    const int h = (int)lane * PULL_PER_LANE + r;
+                    ln[r] = (h < nh && w.hpar[h] < 0) ? w.hl[h] : 0u;
+                    lsum += ln[r];
+                }
+                uint32_t x = lsum;
+#pragma unroll
+                for (int o = 1; o < 32; o <<= 1) {
+                    const uint32_t y = __shfl_up_sync(GRX_FULL_MASK, x, o);
+                    if (lane >= (unsigned)o) x += y;
+                }
+                const uint32_t total = __shfl_sync(GRX_FULL_MASK, x, 31);
+                if (total == 0) break;
+                uint32_t off = x - lsum;
+#pragma unroll
+                for (int r = 0; r < PULL_PER_LANE; ++r) {
+                    const int h = (int)lane * PULL_PER_LANE + r;
+                    if (h < nh) w.hofs[h] = off;
+                    off += ln[r];
+                }
+                if (lane == 0) w.hofs[nh] = total;
+                __syncwarp();
+                const uint32_t steplen = min(total, (uint32_t)PULL_HSTEP);
+                int hrow[PULL_HITEMS];
+                tile_rows(w.hrid, w.hofs, 0u, nh, hrow);
+                const uint32_t j0 = lane * PULL_HITEMS;
+                int32_t uu[PULL_HITEMS];
+#pragma unroll
+                for (int k = 0; k < PULL_HITEMS; ++k) {
+                    const uint32_t j = j0 + k;
+                    const int h = hrow[k];
+                    uu[k] = j < steplen ? __ldg(a.col + w.hb[h] + (OffT)(j - w.hofs[h])) : -1;
+                }
+#pragma unroll
+                for (int k = 0; k < PULL_HITEMS; ++k) {
+                    if (uu[k] >= 0 && ((__ldca(Fin + (uu[k] >> 5)) >> (uu[k] & 31)) & 1u))
+                        w.hpar[hrow[k]] = uu[k];          // any hit is a valid parent
+                }
+                if (STATS && j0 < steplen)
+                    scanned_e += (unsigned long long)min((uint32_t)PULL_HITEMS, steplen - j0);
+                __syncwarp();
+                // the step consumed the first steplen edges of the concatenation
+#pragma unroll
+                for (int r = 0; r < PULL_PER_LANE; ++r) {
+                    const int h = (int)lane * PULL_PER_LANE + r;
+                    if (ln[r] > 0 && w.hpar[h] < 0) {
+                        const uint32_t o = w.hofs[h];
+                        const uint32_t used = steplen > o ? min(ln[r], steplen - o) : 0u;
+                        w.hb[h] += (OffT)used;
+                        w.hl[h] = ln[r] - used;
                     }
                 }
+                __syncwarp();
             }
-            if (h < nh && gl == 0) w.hpar[h] = found;
-        }
-        __syncwarp();
-        // 4. label the found vertices; append found / still-unvisited
-        uint32_t fmask = 0, smask = 0;
-        uint32_t deg[PULL_PER_LANE];
+            // 4. label the found vertices; their bits go to the chunk's word masks
 #pragma unroll
-        for (int k = 0; k < PULL_PER_LANE; ++k) {
-            if (heavy >> k & 1u) par[k] = w.hpar[hpos[k]];
-            deg[k] = (uint32_t)(e[k] - b[k]);
-            const bool fnd = v[k] >= 0 && par[k] >= 0;
-            if (fnd) {
-                a.depth[v[k]] = L + 1;
-                if (PARENT) a.parent[v[k]] = par[k];
-                fmask |= 1u << k;
-            } else if (v[k] >= 0) {
-                smask |= 1u << k;
-            }
-            if (first) {
-                // slot k of every lane lies in the same bitmap word: one atomic per word
-                const uint32_t bits = __reduce_or_sync(GRX_FULL_MASK, fnd ? 1u << lane : 0u);
-                if (lane == 0 && bits) {
-                    const int64_t wd = c * PULL_PER_LANE + k;
-                    atomicOr(a.visited + wd, bits);
-                    if (st.fwrite) atomicOr(Fout + wd, bits);
+            for (int k = 0; k < PULL_PER_LANE; ++k) {
+                if (heavy >> k & 1u) par[k] = w.hpar[hpos[k]];
+                if (v[k] >= 0 && par[k] >= 0) {
+                    a.depth[v[k]] = L + 1;
+                    if (PARENT) a.parent[v[k]] = par[k];
+                    atomicOr(&w.fb[(v[k] >> 5) & 31], 1u << (v[k] & 31));
+                    nfound += 1;
+                    nedges += deg[k];
                 }
-            } else if (fnd) {
-                const uint32_t bit = 1u << (v[k] & 31);
-                atomicOr(a.visited + (v[k] >> 5), bit);
-                if (st.fwrite) atomicOr(Fout + (v[k] >> 5), bit);
             }
+            __syncwarp();
         }
-        warp_append_items<PULL_PER_LANE, OffT>(v, deg, b, fmask, Qv_out, Qe_out, Qr_out, ctr);
-        warp_append_list_items<PULL_PER_LANE>(v, smask, Uout, uctr);
+        if (own) {
+            const uint32_t fb = w.fb[lane];
+            if (fb) a.visited[wd] = vis | fb;
+            Fout[wd] = fb;               // whole word: F_{L+1} needs no clearing first
+        }
         __syncwarp();
     }
+    // one counter update per warp: (found << 32 | their edges)
+    const unsigned long long cnt = warp_sum((unsigned long long)nfound);
+    const unsigned long long edg = warp_sum((unsigned long long)nedges);
+    if (lane == 0 && cnt) atomicAdd(&a.ctl->qpack[(L + 1) & 3], (cnt << 32) | edg);
 }
 
 template <typename OffT, bool PARENT, bool STATS>
-__device__ void run_level(const BfsArgs<OffT> &a, const LevelState &st, WarpSmem<OffT> &w) {
+__device__ void run_phase(const BfsArgs<OffT> &a, const LevelState &st, WarpSmem<OffT> &w) {
     const int L = st.L;
+    const int op = level_op(st);
     if (blockIdx.x == 0 && threadIdx.x == 0) {
-        a.ctl->qpack[(L + 2) & 3] = 0ull;
-        a.ctl->ucount[(L + 2) & 3] = 0u;
-        if (STATS && L < GRX_MAX_LEVELS_STATS) {
-            a.stats->level_t0[L] = grx_globaltimer();
-            a.stats->dir[L] = st.dir;
-            a.stats->frontier[L] = st.q;
-            a.stats->levels = L + 1;
-            if (st.dir == DIR_PUSH) {
-                a.stats->edges_examined[L] = st.T;
-                a.stats->vertices_scanned[L] = st.q;
+        // the compaction counter is only used by a first phase; zero it in a last one
+        if ((int)st.phase + 1 == level_phases(st)) a.ctl->cpack = 0ull;
+        if (st.phase == 0) {
+            a.ctl->qpack[(L + 2) & 3] = 0ull;
+            if (STATS && L < GRX_MAX_LEVELS_STATS) {
+                a.stats->level_t0[L] = grx_globaltimer();
+                a.stats->dir[L] = st.dir;
+                a.stats->frontier[L] = st.q;
+                a.stats->levels = L + 1;
+                if (st.dir == DIR_PUSH) {
+                    a.stats->edges_examined[L] = st.T;
+                    a.stats->vertices_scanned[L] = st.q;
+                }
             }
         }
     }
-    if (st.fclear) {
-        // F_{L-1} only holds bits of Q_{L-1}'s vertices: zero their words.
-        const int32_t *Qp = pick3(a.Q[0], a.Q[1], a.Q[2], (L + 2) % 3);
+    if (st.phase == 0 && st.fclear && st.dir == DIR_PUSH) {
+        // zero F_{L-1} (pull levels do it in their word loop)
         uint32_t *Fp = pick3(a.F[0], a.F[1], a.F[2], (L + 2) % 3);
-        for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < (int64_t)st.qprev;
-             i += (int64_t)gridDim.x * blockDim.x)
-            Fp[__ldcg(Qp + i) >> 5] = 0u;
+        if (st.qprev_ok) {
+            // F_{L-1} only holds bits of Q_{L-1}'s vertices: zero their words
+            const int32_t *Qp = pick3(a.Q[0], a.Q[1], a.Q[2], (L + 2) % 3);
+            for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < (int64_t)st.nprev;
+                 i += (int64_t)gridDim.x * blockDim.x)
+                Fp[__ldcg(Qp + i) >> 5] = 0u;
+        } else {
+            for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < a.words;
+                 i += (int64_t)gridDim.x * blockDim.x)
+                Fp[i] = 0u;
+        }
     }
-    if (st.dir == DIR_PUSH) {
-        push_level<OffT, PARENT, STATS>(a, st, w.p);
-    } else {
+    switch (op) {
+    case OP_QPUSH: push_queue<OffT, PARENT>(a, st, w.p); break;
+    case OP_BMARK: push_mark<OffT, PARENT>(a, st, w.p); break;
+    case OP_BFINAL: bitmap_to_queue<OffT, true>(a, st, w.l); break;
+    case OP_COMPACT: bitmap_to_queue<OffT, false>(a, st, w.l); break;
+    default: {
         unsigned long long scanned_e = 0, scanned_v = 0;
         pull_level<OffT, PARENT, STATS>(a, st, w.l, scanned_e, scanned_v);
         if (STATS) {
@@ -510,12 +769,13 @@ __device__ void run_level(const BfsArgs<OffT> &a, const LevelState &st, WarpSmem
             }
         }
     }
+    }
 }
 
 // Phase 0 of a traversal: depth = -1 (0 at src), parent = -1 (src at src),
-// visited = {src}, frontier bitmaps = {src} / empty, the frontier counters
-// and the first frontier slot.  Every word is written by exactly one thread,
-// so clearing and seeding need no barrier between them.
+// visited = {src}, F_0 = {src}, the other frontier bitmaps empty, the
+// counters and the first frontier slot.  Every word is written by exactly one
+// thread, so clearing and seeding need no barrier between them.
 template <typename OffT, bool PARENT>
 __device__ void init_phase(const BfsArgs<OffT> &a, const LevelState &st0) {
     const int64_t tid = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
@@ -527,14 +787,11 @@ __device__ void init_phase(const BfsArgs<OffT> &a, const LevelState &st0) {
     }
     const int64_t sw = src >> 5;
     const uint32_t sb = 1u << (src & 31);
-    const bool use_f = a.mode != GRX_DIR_PUSH;
     for (int64_t w = tid; w < a.words; w += stride) {
         a.visited[w] = w == sw ? sb : 0u;
-        if (use_f) {
-            a.F[0][w] = (w == sw && st0.q) ? sb : 0u;
-            a.F[1][w] = 0u;
-            a.F[2][w] = 0u;
-        }
+        a.F[0][w] = w == sw ? sb : 0u;
+        a.F[1][w] = 0u;
+        a.F[2][w] = 0u;
     }
     if (tid == 0) {
         a.Q[0][0] = src;
@@ -542,7 +799,7 @@ __device__ void init_phase(const BfsArgs<OffT> &a, const LevelState &st0) {
         a.R[0][0] = __ldg(a.ro + src);
         a.ctl->qpack[0] = st0.q ? ((1ull << 32) | st0.T) : 0ull;
         for (int i = 1; i < 4; ++i) a.ctl->qpack[i] = 0ull;
-        for (int i = 0; i < 4; ++i) a.ctl->ucount[i] = 0u;
+        a.ctl->cpack = 0ull;
     }
 }
 
@@ -559,7 +816,7 @@ __global__ void __launch_bounds__(BFS_BLOCK, 3) k_bfs_persistent(BfsArgs<OffT> a
     for (;;) {
         const LevelState st = s_st;
         if (st.done) break;
-        run_level<OffT, PARENT, STATS>(a, st, w);
+        run_phase<OffT, PARENT, STATS>(a, st, w);
         if (!flag_barrier(bar)) return;
         if (threadIdx.x == 0) s_st = next_state(a, st, STATS);
         __syncthreads();
@@ -570,8 +827,8 @@ __global__ void __launch_bounds__(BFS_BLOCK, 3) k_bfs_persistent(BfsArgs<OffT> a
     }
 }
 
-// Host-stepped variant: launch 0 initialises, launch i >= 1 runs level i-1.
-// The state of a level is derived at the start of its launch from the state
+// Host-stepped variant: launch 0 initialises, launch i >= 1 runs phase i-1.
+// The state of a phase is derived at the start of its launch from the state
 // the previous launch stored and the counters it left, so no block ever
 // waits on another.
 template <typename OffT, bool PARENT, bool STATS>
@@ -601,11 +858,11 @@ __global__ void __launch_bounds__(BFS_BLOCK) k_bfs_step(BfsArgs<OffT> a, int lau
         if (st.done) a.ctl->levels_run = st.L;
     }
     if (st.done) return;
-    run_level<OffT, PARENT, STATS>(a, st, wsm[threadIdx.x >> 5]);
+    run_phase<OffT, PARENT, STATS>(a, st, wsm[threadIdx.x >> 5]);
 }
 
-// CUDA-graph variant: the body of a device-evaluated WHILE node is one level
-// kernel followed by a one-thread tick that derives the next level's state
+// CUDA-graph variant: the body of a device-evaluated WHILE node is one phase
+// kernel followed by a one-thread tick that derives the next phase's state
 // and sets the loop condition.  The arguments live in device memory so one
 // instantiated graph serves every call on the graph.
 template <typename OffT, bool PARENT>
@@ -617,7 +874,7 @@ __global__ void __launch_bounds__(BFS_BLOCK) k_bfs_glevel(const BfsArgs<OffT> *a
     __syncthreads();
     const LevelState st = s_st;
     if (st.done) return;
-    run_level<OffT, PARENT, false>(a, st, wsm[threadIdx.x >> 5]);
+    run_phase<OffT, PARENT, false>(a, st, wsm[threadIdx.x >> 5]);
 }
 
 template <typename OffT>
@@ -648,8 +905,6 @@ BfsArgs<OffT> make_args(grx_graph *g, int32_t src, int32_t *depth, int32_t *pare
         a.E[i] = g->qe[i];
         a.R[i] = (OffT *)g->qr[i];
     }
-    a.U[0] = g->ulist[0];
-    a.U[1] = g->ulist[1];
     a.depth = depth;
     a.parent = parent;
     a.ctl = g->ctl;
@@ -659,6 +914,14 @@ BfsArgs<OffT> make_args(grx_graph *g, int32_t src, int32_t *depth, int32_t *pare
     a.exact_fv = o->exact_fv;
     a.alpha = o->alpha;
     a.beta = o->beta;
+    // bitmap push when a level's edges reach push_bitmap * nv (0 = 1/8, < 0 = never)
+    const double pb = o->push_bitmap == 0.f ? 0.125 : (double)o->push_bitmap;
+    if (pb < 0) {
+        a.bmp_min_T = 0xffffffffu;
+    } else {
+        const double t = pb * (double)g->nv;
+        a.bmp_min_T = t < 1.0 ? 1u : (t > 4294967295.0 ? 0xffffffffu : (uint32_t)t);
+    }
     a.timeout_ns = grx_timeout_ns(o);
     a.src = src;
     return a;
@@ -737,11 +1000,13 @@ grx_status launch_typed(grx_graph *g, int32_t src, int32_t *depth, int32_t *pare
     }
     if (o->loop == GRX_LOOP_HOST) {
         int blocks = o->grid_blocks > 0 ? o->grid_blocks : g->ctx->num_sms * 4;
-        // Poll the done flag every 16 launches; a traversal has at most nv levels.
+        // Poll the done flag every 16 launches; a traversal has at most nv
+        // levels of at most 3 phases each.
         long long st_host[8];
         if (o->ev_begin) GRX_CUDA(cudaEventRecord((cudaEvent_t)o->ev_begin, s));
-        for (int launch = 0; launch <= g->nv + 1; ++launch) {
-            k_bfs_step<OffT, PARENT, STATS><<<blocks, BFS_BLOCK, 0, s>>>(a, launch);
+        const long long max_launch = 3ll * ((long long)g->nv + 1) + 1;
+        for (long long launch = 0; launch <= max_launch; ++launch) {
+            k_bfs_step<OffT, PARENT, STATS><<<blocks, BFS_BLOCK, 0, s>>>(a, (int)launch);
             if ((launch & 15) == 15) {
                 GRX_CUDA(cudaMemcpyAsync(st_host, (const void *)g->ctl->hstate[launch & 1],
                                          sizeof st_host, cudaMemcpyDeviceToHost, s));

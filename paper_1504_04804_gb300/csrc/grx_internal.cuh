@@ -28,7 +28,8 @@ struct alignas(128) TravCtl {
     unsigned int disc[4];            // vertices discovered per level, same ring
     int status;                      // first device-side error (0 = ok)
     int levels_run;                  // levels completed by the last traversal
-    unsigned int pad0[18];
+    unsigned long long cpack;        // BFS bitmap->queue compaction counter (count << 32 | edges)
+    unsigned int pad0[16];
     unsigned int bar_count;          // grid barrier arrivals
     unsigned int pad1[31];
     unsigned int bar_gen;            // grid barrier generation

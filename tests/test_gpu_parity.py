@@ -61,18 +61,29 @@ def loaded(grx):
     return {name: grx.load(g, validate=True) for name, g in GRAPHS.items()}
 
 
+# push levels: library default threshold, bitmap marking on every push
+# level, queue push only
+PUSH_BITMAP = {"pbdefault": 0.0, "pbalways": 1e-9, "pbnever": -1.0}
+
+
 @pytest.mark.parametrize("name", list(GRAPHS))
 @pytest.mark.parametrize("mode", list(MODES))
-def test_bfs_matches_oracle(grx, loaded, name, mode):
+@pytest.mark.parametrize("pb", list(PUSH_BITMAP))
+def test_bfs_matches_oracle(grx, loaded, name, mode, pb):
     g, dg = GRAPHS[name], loaded[name]
-    o = grx.opts(direction=MODES[mode])
+    o = grx.opts(direction=MODES[mode], push_bitmap=PUSH_BITMAP[pb])
     for s in _sources(g, 4) + [g.nv - 1]:
-        d, p = grx.bfs(dg, s, opts=o, parent=True)
-        grx.graph_status(dg)
-        want = oracle.bfs(g.row_offsets, g.col_indices, s)
-        got = d.cpu().numpy()
-        assert np.array_equal(got, want), (name, mode, s, np.flatnonzero(got != want)[:10])
-        assert oracle.check_bfs(g.row_offsets, g.col_indices, s, got, p.cpu().numpy()) == 0
+        for want_parent in (True, False):
+            if want_parent:
+                d, p = grx.bfs(dg, s, opts=o, parent=True)
+            else:
+                d = grx.bfs(dg, s, opts=o)
+            grx.graph_status(dg)
+            want = oracle.bfs(g.row_offsets, g.col_indices, s)
+            got = d.cpu().numpy()
+            assert np.array_equal(got, want), (name, mode, pb, s, np.flatnonzero(got != want)[:10])
+            if want_parent:
+                assert oracle.check_bfs(g.row_offsets, g.col_indices, s, got, p.cpu().numpy()) == 0
 
 
 @pytest.mark.parametrize("alpha,beta,exact", [(0.01, 0.1, 0), (1e-4, 1e-3, 0), (0.5, 0.05, 0),
@@ -106,13 +117,13 @@ def test_bfs_host_stepped_and_cuda_graph_loops(grx, loaded, loop):
     mode = grx.GRX_LOOP_HOST if loop == "host" else grx.GRX_LOOP_GRAPH
     for name in ("rmat10", "path", "grid64", "star", "disconnected"):
         g, dg = GRAPHS[name], loaded[name]
-        for direction in (0, 1, 2):
-            o = grx.opts(loop=mode, direction=direction)
+        for direction, pb in itertools.product((0, 1, 2), (0.0, 1e-9, -1.0)):
+            o = grx.opts(loop=mode, direction=direction, push_bitmap=pb)
             for s in _sources(g, 2, seed=2) + [g.nv - 1]:
                 d, p = grx.bfs(dg, s, opts=o, parent=True)
                 grx.graph_status(dg)
                 want = oracle.bfs(g.row_offsets, g.col_indices, s)
-                assert np.array_equal(d.cpu().numpy(), want), (loop, name, direction, s)
+                assert np.array_equal(d.cpu().numpy(), want), (loop, name, direction, pb, s)
                 assert oracle.check_bfs(g.row_offsets, g.col_indices, s, d.cpu().numpy(),
                                         p.cpu().numpy()) == 0
 
@@ -174,8 +185,8 @@ def test_exhaustive_6_vertex_graphs_as_one_union(grx):
     rng = np.random.default_rng(6)
     for gi in rng.choice(1 << 15, size=64, replace=False):
         s = int(6 * gi + rng.integers(0, 6))
-        for mode in (0, 1, 2):
-            d = grx.bfs(du, s, opts=grx.opts(direction=mode)).cpu().numpy()
+        for mode, pb in itertools.product((0, 1, 2), (0.0, 1e-9)):
+            d = grx.bfs(du, s, opts=grx.opts(direction=mode, push_bitmap=pb)).cpu().numpy()
             assert np.array_equal(d, oracle.bfs(u.row_offsets, u.col_indices, s))
         dist = grx.as_uint32(grx.sssp(du, s))
         assert np.array_equal(dist, oracle.sssp(u.row_offsets, u.col_indices, u.weights, s))
