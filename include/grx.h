@@ -126,11 +126,12 @@ typedef struct {
                              the paper's |Q|*E/V estimate */
     void *ev_begin;       /* optional cudaEvent_t recorded on `stream` just  */
     void *ev_end;         /* before / after the traversal kernel(s) (timing) */
-    float push_bitmap;    /* BFS push levels with at least push_bitmap * nv
-                             frontier edges mark their targets in a bitmap and
-                             build the next frontier in a second pass (no
-                             per-edge atomic with a return value); 0 = 1/8,
-                             < 0 = never.  Results do not depend on it. */
+    float push_bitmap;    /* BFS and multi-source BFS push levels with at
+                             least push_bitmap * nv frontier edges mark their
+                             targets in a bitmap and build the next frontier
+                             in a second pass (no per-edge atomic with a
+                             return value); 0 = 1/8, < 0 = never.  Results do
+                             not depend on it. */
 } grx_opts;
 
 /* Library defaults: AUTO direction, alpha 0.01, beta 0.1 (Sec. 6.1's values

@@ -82,13 +82,16 @@ __global__ void k_edge_tiles(const uint32_t *aoff, int64_t n_active, int64_t ne,
 }  // namespace
 
 grx_status grx_edge_tiles(grx_graph *g, int tile, cudaStream_t s, const int2 **out) {
-    for (int i = 0; i < 2; ++i)
+    const int nslots = (int)(sizeof g->etiles / sizeof g->etiles[0]);
+    int slot = -1;
+    for (int i = 0; i < nslots; ++i) {
         if (g->etiles[i] && g->etile_size[i] == tile) {
             *out = g->etiles[i];
             return GRX_OK;
         }
-    int slot = g->etiles[0] ? 1 : 0;
-    if (g->etiles[slot]) return grx_fail(GRX_EINVAL, "edge tiles: more than two tile sizes requested");
+        if (!g->etiles[i] && slot < 0) slot = i;
+    }
+    if (slot < 0) return grx_fail(GRX_EINVAL, "edge tiles: too many tile sizes requested");
     const int64_t ntiles = (g->ne + tile - 1) / tile;
     int2 *p = (int2 *)grx_alloc(g, (size_t)(ntiles > 0 ? ntiles : 1) * sizeof(int2), s);
     if (!p) return grx_fail(GRX_ENOMEM, "edge tiles: allocation failed");

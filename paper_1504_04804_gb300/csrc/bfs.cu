@@ -228,29 +228,6 @@ __device__ LevelState next_state(const BfsArgs<OffT> &a, const LevelState &st, b
     return ns;
 }
 
-// Compacts the set bits of a 32-word bitmap chunk (lane i holds word i) into
-// list[] as chunk offsets (word * 32 + bit) in increasing order.  Returns the
-// count in every lane.
-__device__ __forceinline__ int warp_compact_bits(uint32_t bits, uint16_t *list) {
-    const unsigned int lane = threadIdx.x & 31;
-    const int c = __popc(bits);
-    int x = c;
-#pragma unroll
-    for (int o = 1; o < 32; o <<= 1) {
-        const int y = __shfl_up_sync(GRX_FULL_MASK, x, o);
-        if (lane >= (unsigned)o) x += y;
-    }
-    const int total = __shfl_sync(GRX_FULL_MASK, x, 31);
-    int pos = x - c;
-    while (bits) {
-        const int b = __ffs(bits) - 1;
-        bits &= bits - 1;
-        list[pos++] = (uint16_t)(lane * 32 + b);
-    }
-    __syncwarp();
-    return total;
-}
-
 // Row of every position of a warp tile, without per-item searches or loops
 // (branches are the scarce resource of a hot tile loop): positions start at
 // row 0; each non-empty row j > 0 that starts inside the tile writes j at its

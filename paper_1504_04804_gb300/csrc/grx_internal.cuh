@@ -29,7 +29,9 @@ struct alignas(128) TravCtl {
     int status;                      // first device-side error (0 = ok)
     int levels_run;                  // levels completed by the last traversal
     unsigned long long cpack;        // BFS bitmap->queue compaction counter (count << 32 | edges)
-    unsigned int pad0[16];
+    unsigned int ms_grid;            // multi-source BFS: grid of the last traversal
+    unsigned int ms_done;            // ... blocks that completed its final pass
+    unsigned int pad0[14];
     unsigned int bar_count;          // grid barrier arrivals
     unsigned int pad1[31];
     unsigned int bar_gen;            // grid barrier generation
@@ -75,9 +77,10 @@ struct grx_graph {
     int32_t *active;
     uint32_t *aoff;
     int64_t n_active;
-    // static row ranges of all-edges tiles (CC hooking, PageRank), per tile size
-    int2 *etiles[2];
-    int etile_size[2];
+    // static row ranges of all-edges tiles (CC hooking, PageRank, multi-source
+    // pull), per tile size
+    int2 *etiles[4];
+    int etile_size[4];
     void *last_stream;
     // ---- traversal workspace (allocated on first use) ----
     int ws_ready;
@@ -99,6 +102,10 @@ struct grx_graph {
     int64_t pr_fix_len;
     // multi-source
     unsigned long long *ms_cur[3], *ms_next, *ms_seen;   // [nv] each
+    unsigned long long *ms_hist[6];  // multi-source BFS: pull levels' new lanes, [nv] each
+    int32_t *ms_fix;                 // multi-source BFS: per pull tile, the crossing row it finishes
+    uint32_t *ms_tbits;              // multi-source BFS: touched bitmap of bitmap push levels
+    uint8_t *ms_sat;                 // multi-source BFS: per pull tile, all lanes seen
     uint32_t *ms_dist;               // batched SSSP, vertex-major [nv][64]
     int ms_ready;
     // CUDA-graph level loop of bfs (GRX_LOOP_GRAPH), per parent flag
@@ -473,6 +480,29 @@ __device__ __forceinline__ void block_scan3(uint32_t a, uint32_t b, uint32_t c, 
     ea = px + x - a; eb = py + y - b; ec = pz + z - c;
     ta = sx; tb = sy; tc = sz;
     __syncthreads();
+}
+
+// Compacts the set bits of a 32-word bitmap chunk (lane i holds word i) into
+// list[] as chunk offsets (word * 32 + bit) in increasing order.  Returns the
+// count in every lane.
+__device__ __forceinline__ int warp_compact_bits(uint32_t bits, uint16_t *list) {
+    const unsigned int lane = threadIdx.x & 31;
+    const int c = __popc(bits);
+    int x = c;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const int y = __shfl_up_sync(GRX_FULL_MASK, x, o);
+        if (lane >= (unsigned)o) x += y;
+    }
+    const int total = __shfl_sync(GRX_FULL_MASK, x, 31);
+    int pos = x - c;
+    while (bits) {
+        const int b = __ffs(bits) - 1;
+        bits &= bits - 1;
+        list[pos++] = (uint16_t)(lane * 32 + b);
+    }
+    __syncwarp();
+    return total;
 }
 
 template <typename T>

@@ -272,14 +272,33 @@ def test_timeout_status_is_reported_and_context_survives(grx, loaded):
 
 @pytest.mark.parametrize("name", ["rmat10", "rmat13", "rmat14_ef4", "grid64", "path", "star", "disconnected"])
 @pytest.mark.parametrize("mode", list(MODES))
-def test_bfs_multi_lanes_match_oracle(grx, loaded, name, mode):
+@pytest.mark.parametrize("pb", ["pbdefault", "pbalways", "pbnever"])
+def test_bfs_multi_lanes_match_oracle(grx, loaded, name, mode, pb):
     g, dg = GRAPHS[name], loaded[name]
     srcs = _sources(g, 61, seed=7) if name != "disconnected" else [1, 5, 10, 30, 0, 2]
     srcs = (srcs + [srcs[0], g.nv - 1, srcs[-1]])[:64]          # duplicates and an isolated/last vertex
-    d = grx.bfs_multi(dg, srcs, opts=grx.opts(direction=MODES[mode])).cpu().numpy()
+    o = grx.opts(direction=MODES[mode], push_bitmap=PUSH_BITMAP[pb])
+    d = grx.bfs_multi(dg, srcs, opts=o).cpu().numpy()
     grx.graph_status(dg)
     for b, s in enumerate(srcs):
-        assert np.array_equal(d[b], oracle.bfs(g.row_offsets, g.col_indices, s)), (name, mode, b, s)
+        assert np.array_equal(d[b], oracle.bfs(g.row_offsets, g.col_indices, s)), (name, mode, pb, b, s)
+
+
+def test_bfs_multi_after_an_interrupted_traversal(grx, loaded):
+    """A multi-source traversal cut short by its wait limit leaves scratch
+    state behind; the next one must clear it and still be exact."""
+    for name, mode in (("path", 2), ("rmat13", 0), ("grid64", 1)):
+        g, dg = GRAPHS[name], loaded[name]
+        srcs = _sources(g, 40, seed=11)
+        grx.bfs_multi(dg, srcs, opts=grx.opts(timeout_s=1e-9, direction=mode))
+        try:
+            grx.graph_status(dg)
+        except grx.GrxError as e:
+            assert e.status == grx.GRX_ETIMEOUT
+        d = grx.bfs_multi(dg, srcs, opts=grx.opts(direction=mode)).cpu().numpy()
+        grx.graph_status(dg)
+        for b, s in enumerate(srcs):
+            assert np.array_equal(d[b], oracle.bfs(g.row_offsets, g.col_indices, s)), (name, b, s)
 
 
 def test_bfs_multi_few_lanes_and_stats(grx, loaded):
