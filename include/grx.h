@@ -179,6 +179,16 @@ grx_status cc(grx_graph *g, int32_t *label_out, void *stream);
  * rank_out: device float[nv].  FP32 arithmetic. */
 grx_status pagerank(grx_graph *g, float damping, int iters, float *rank_out, void *stream);
 
+/* grx_pagerank_block -- column-block width of pagerank's gathers.  When the
+ * contribution array (4*nv bytes) outgrows L2, each iteration runs one pass
+ * per block of 2^shift columns over the row segments that fall in it, so the
+ * gathers of a pass hit a slice that stays in L2.  shift <= 0 = no blocks
+ * (the default: measured faster on GB300 up to R-MAT scale 26), else 2^shift
+ * vertices (must give at most 256 blocks: GRX_EINVAL otherwise).
+ * The segment tables (12 bytes per segment) are built on the next pagerank
+ * call.  Results agree within the FP32 tolerance either way. */
+grx_status grx_pagerank_block(grx_graph *g, int shift);
+
 /* ---- allocation-free BFS ---------------------------------------------------
  * bfs_noalloc -- the same traversal as bfs(), for callers that cannot allocate
  * device memory (a host framework that owns the GPU's memory pool and forbids

@@ -452,6 +452,16 @@ extern "C" grx_status pagerank(grx_graph *g, float damping, int iters, float *ra
     return grx_pr_launch(g, damping, iters, rank_out, (cudaStream_t)stream);
 }
 
+extern "C" grx_status grx_pagerank_block(grx_graph *g, int shift) {
+    grx_status st = check_graph(g, "grx_pagerank_block");
+    if (st) return st;
+    if (shift > 0 && (shift > 31 || (((int64_t)g->nv + (1ll << shift) - 1) >> shift) > GRX_PRB_MAX_K))
+        return grx_fail(GRX_EINVAL, "grx_pagerank_block: 2^%d-vertex blocks give more than %d blocks", shift,
+                        GRX_PRB_MAX_K);
+    g->pr_shift_req = shift;
+    return GRX_OK;
+}
+
 
 static grx_status check_sources(grx_graph *g, const int32_t *srcs, int n, const char *who) {
     if (!srcs) return grx_fail(GRX_EINVAL, "%s: srcs is NULL", who);

@@ -50,6 +50,8 @@ struct alignas(128) TravCtl {
 
 // Maximum grid of the persistent kernels (size of the barrier flag array).
 #define GRX_MAX_GRID 4096
+// PageRank column blocks: at most this many.
+#define GRX_PRB_MAX_K 256
 
 struct DevStats {                    // device mirror of grx_trav_stats
     int32_t levels;
@@ -100,6 +102,16 @@ struct grx_graph {
     float *pr_s;                     // cross-tile partial sums
     int32_t *pr_fix;                 // per-tile row needing a fix-up
     int64_t pr_fix_len;
+    // PageRank column blocks (segments of rows per block of 2^prb_shift columns)
+    int pr_shift_req;                // requested block width (0 = automatic, < 0 = never)
+    int prb_K, prb_shift;            // built blocks (prb_K < 2: none)
+    int32_t *prb_seg_v;              // segment's row vertex
+    uint32_t *prb_seg_start;         // segment's first edge
+    uint32_t *prb_pre;               // per block: exclusive edge prefix (+ sentinel)
+    int2 *prb_tiles;                 // per block: equal edge tiles (first segment, count)
+    int64_t prb_kbase[GRX_PRB_MAX_K + 1];
+    int64_t prb_tbase[GRX_PRB_MAX_K + 1];
+    uint32_t prb_kedges[GRX_PRB_MAX_K];
     // multi-source
     unsigned long long *ms_cur[3], *ms_next, *ms_seen;   // [nv] each
     unsigned long long *ms_hist[6];  // multi-source BFS: pull levels' new lanes, [nv] each

@@ -11,9 +11,10 @@
 // One launch per iteration over equal tiles of the edge array (the active
 // list of non-isolated vertices has the CSR offsets as its edge prefix, so a
 // tile holds at most TILE+1 rows; the first row and row count of every tile
-// are computed once per graph and cached).  A tile stages c[col[e]] for its edges in shared memory;
-// each thread sums a contiguous run of edges per row and adds its partial to
-// the row's shared accumulator.  Rows inside the tile are finished there;
+// are computed once per graph and cached).  Each thread loads a contiguous
+// run of PR_ITEMS edges' c[col[e]] (all loads in flight before any use),
+// finds their rows by a scatter + max-scan in shared memory, and adds one
+// partial per run of equal rows to the row's shared accumulator.  Rows inside the tile are finished there;
 // rows that cross a tile boundary add their partial to a global accumulator
 // and are finished by a small fix-up launch.  Accumulation is FP32.
 #include <vector>
@@ -27,11 +28,71 @@ constexpr int PR_ITEMS = 9;                  // odd: conflict-free strided smem 
 constexpr int PR_TILE = PR_BLOCK * PR_ITEMS;
 
 struct PrSmem {
-    float val[PR_TILE];
     float acc[PR_TILE + 2];
     uint32_t qe[PR_TILE + 2];
     int32_t u[PR_TILE + 2];
+    uint16_t rid[PR_TILE];
+    int wmax[PR_BLOCK / 32];
 };
+
+// Row of each of a thread's PR_ITEMS consecutive tile positions, with no
+// per-item search: positions start at row 0; every row j > 0 writes j at its
+// first position (starts[j] - origin, strictly increasing for rows with
+// edges); an inclusive max-scan over positions (per thread, then across the
+// block's threads) gives each position its row.  All threads call.
+__device__ __forceinline__ void block_tile_rows(uint16_t *rid, int *wmax, const uint32_t *starts,
+                                                uint32_t origin, int n, int len, int (&row)[PR_ITEMS]) {
+    const int t0 = threadIdx.x * PR_ITEMS;
+#pragma unroll
+    for (int k = 0; k < PR_ITEMS; ++k) rid[t0 + k] = 0;
+    __syncthreads();
+    for (int j = 1 + threadIdx.x; j < n; j += PR_BLOCK) {
+        const uint32_t p = starts[j] - origin;
+        if (p < (uint32_t)len) rid[p] = (uint16_t)j;
+    }
+    __syncthreads();
+    int m = 0;
+#pragma unroll
+    for (int k = 0; k < PR_ITEMS; ++k) {
+        m = max(m, (int)rid[t0 + k]);
+        row[k] = m;
+    }
+    const unsigned int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    int x = m;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const int y = __shfl_up_sync(GRX_FULL_MASK, x, o);
+        if (lane >= (unsigned)o) x = max(x, y);
+    }
+    if (lane == 31) wmax[wid] = x;
+    __syncthreads();
+    int carry = __shfl_up_sync(GRX_FULL_MASK, x, 1);
+    if (lane == 0) carry = 0;
+    for (unsigned int w = 0; w < wid; ++w) carry = max(carry, wmax[w]);
+#pragma unroll
+    for (int k = 0; k < PR_ITEMS; ++k) row[k] = max(row[k], carry);
+}
+
+// Adds each item's value to its row's shared accumulator, one atomic per run
+// of equal rows (rows of a thread's items are non-decreasing).
+__device__ __forceinline__ void add_runs(float *acc, const int (&row)[PR_ITEMS], const float (&g)[PR_ITEMS],
+                                         int valid) {
+    if (valid <= 0) return;
+    int cj = row[0];
+    float part = 0.f;
+#pragma unroll
+    for (int k = 0; k < PR_ITEMS; ++k) {
+        if (k < valid) {
+            if (row[k] != cj) {
+                atomicAdd(&acc[cj], part);
+                part = 0.f;
+                cj = row[k];
+            }
+            part += g[k];
+        }
+    }
+    atomicAdd(&acc[cj], part);
+}
 
 __global__ void __launch_bounds__(PR_BLOCK) k_pr_iter(
     const int32_t *__restrict__ col, const int32_t *__restrict__ active,
@@ -43,6 +104,14 @@ __global__ void __launch_bounds__(PR_BLOCK) k_pr_iter(
     const uint64_t e0 = tile * PR_TILE;
     const uint64_t e1 = min((uint64_t)ne, e0 + PR_TILE);
     const int len = (int)(e1 - e0);
+    const int t0 = threadIdx.x * PR_ITEMS;
+    // the gathers need no row: all of a thread's loads go out first
+    int32_t u[PR_ITEMS];
+#pragma unroll
+    for (int k = 0; k < PR_ITEMS; ++k) u[k] = t0 + k < len ? __ldg(col + e0 + t0 + k) : -1;
+    float g[PR_ITEMS];
+#pragma unroll
+    for (int k = 0; k < PR_ITEMS; ++k) g[k] = u[k] >= 0 ? __ldg(c_in + u[k]) : 0.f;
     const int2 tr = __ldg(tiles + tile);
     const int64_t i0 = tr.x;
     const int n = tr.y;
@@ -52,27 +121,10 @@ __global__ void __launch_bounds__(PR_BLOCK) k_pr_iter(
         if (j < n) sm.u[j] = __ldg(active + i0 + j);
         sm.acc[j] = 0.f;
     }
-    for (int k = threadIdx.x; k < len; k += PR_BLOCK) sm.val[k] = __ldg(c_in + __ldg(col + e0 + k));
     __syncthreads();
-    // contiguous run of PR_ITEMS edges per thread
-    const int t0 = threadIdx.x * PR_ITEMS;
-    if (t0 < len) {
-        int j = upper_index_smem(sm.qe, n, (uint32_t)(e0 + t0));
-        uint32_t next_start = sm.qe[j + 1];
-        float part = 0.f;
-        const int t1 = min(len, t0 + PR_ITEMS);
-        for (int k = t0; k < t1; ++k) {
-            const uint32_t e = (uint32_t)(e0 + k);
-            while (e >= next_start) {
-                atomicAdd(&sm.acc[j], part);
-                part = 0.f;
-                ++j;
-                next_start = sm.qe[j + 1];
-            }
-            part += sm.val[k];
-        }
-        atomicAdd(&sm.acc[j], part);
-    }
+    int row[PR_ITEMS];
+    block_tile_rows(sm.rid, sm.wmax, sm.qe, (uint32_t)e0, n, len, row);
+    add_runs(sm.acc, row, g, len - t0);
     __syncthreads();
     for (int j = threadIdx.x; j < n; j += PR_BLOCK) {
         const int32_t v = sm.u[j];
@@ -119,6 +171,261 @@ __global__ void k_pr_fill(const uint32_t *__restrict__ nz, int32_t nv, float val
         if (all || !((nz[v >> 5] >> (v & 31)) & 1u)) rank[v] = value;
 }
 
+// ---------------------------------------------------------------------------
+// Column-blocked gathers.  When the contribution array c is larger than L2,
+// every gather c[col[e]] is a DRAM sector.  The columns are then cut into K
+// blocks of 2^shift vertices; since every row is sorted, its neighbours in
+// block k form one contiguous segment of the row.  Iteration pass k visits
+// the segments of block k only (in row order, in equal edge tiles), so its
+// gathers hit a 4*2^shift-byte slice of c that stays in L2; the per-row sums
+// of the K passes meet in an FP32 accumulator (reductions), and a finishing
+// pass turns them into ranks.  Segments: (row vertex, first edge) plus the
+// per-block edge prefix, built once per graph and block width.
+// ---------------------------------------------------------------------------
+constexpr int PRB_BUILD = 256;
+
+// First position in col[lo, hi) whose value is >= key (sorted row).
+__device__ __forceinline__ uint32_t row_lower_bound(const int32_t *col, uint32_t lo, uint32_t hi,
+                                                    int64_t key) {
+    while (lo < hi) {
+        const uint32_t mid = lo + ((hi - lo) >> 1);
+        if ((int64_t)__ldg(col + mid) < key) lo = mid + 1; else hi = mid;
+    }
+    return lo;
+}
+
+// Per build block and column block: number of non-empty segments and their edges.
+__global__ void __launch_bounds__(PRB_BUILD) k_prb_count(const int32_t *__restrict__ col,
+                                                         const uint32_t *__restrict__ aoff,
+                                                         int64_t n_active, int shift, int K,
+                                                         uint32_t *cnt, uint32_t *es) {
+    extern __shared__ uint32_t sh[];                 // [2K]
+    for (int k = threadIdx.x; k < 2 * K; k += blockDim.x) sh[k] = 0u;
+    __syncthreads();
+    const int64_t i = blockIdx.x * (int64_t)PRB_BUILD + threadIdx.x;
+    if (i < n_active) {
+        const uint32_t e0 = __ldg(aoff + i), e1 = __ldg(aoff + i + 1);
+        uint32_t lo = e0;
+        for (int k = 0; k < K && lo < e1; ++k) {
+            const uint32_t hi = k + 1 < K ? row_lower_bound(col, lo, e1, (int64_t)(k + 1) << shift) : e1;
+            if (hi > lo) {
+                atomicAdd(&sh[k], 1u);
+                atomicAdd(&sh[K + k], hi - lo);
+            }
+            lo = hi;
+        }
+    }
+    __syncthreads();
+    for (int k = threadIdx.x; k < K; k += blockDim.x) {
+        cnt[(int64_t)k * gridDim.x + blockIdx.x] = sh[k];
+        es[(int64_t)k * gridDim.x + blockIdx.x] = sh[K + k];
+    }
+}
+
+// Writes the segments in (column block, row) order.  cpre/epre: per (k, build
+// block) exclusive prefixes of counts and edges within block k; kbase[k]: first
+// segment of block k.  Segment j of block k has its edge prefix at pre[j + k].
+__global__ void __launch_bounds__(PRB_BUILD) k_prb_fill(const int32_t *__restrict__ col,
+                                                        const int32_t *__restrict__ active,
+                                                        const uint32_t *__restrict__ aoff,
+                                                        int64_t n_active, int shift, int K,
+                                                        const uint32_t *cpre, const uint32_t *epre,
+                                                        const int64_t *kbase, int32_t *seg_v,
+                                                        uint32_t *seg_start, uint32_t *pre) {
+    const int64_t i = blockIdx.x * (int64_t)PRB_BUILD + threadIdx.x;
+    const bool ok = i < n_active;
+    const uint32_t e0 = ok ? __ldg(aoff + i) : 0u, e1 = ok ? __ldg(aoff + i + 1) : 0u;
+    const int32_t v = ok ? __ldg(active + i) : 0;
+    uint32_t lo = e0;
+    for (int k = 0; k < K; ++k) {                    // uniform loop: block scans inside
+        uint32_t hi = lo;
+        if (ok && lo < e1) hi = k + 1 < K ? row_lower_bound(col, lo, e1, (int64_t)(k + 1) << shift) : e1;
+        const uint32_t len = hi - lo;
+        uint32_t rc, re, rz, tc, te, tz;
+        block_scan3<PRB_BUILD>(len ? 1u : 0u, len, 0u, rc, re, rz, tc, te, tz);
+        if (len) {
+            const int64_t pos = kbase[k] + cpre[(int64_t)k * gridDim.x + blockIdx.x] + rc;
+            seg_v[pos] = v;
+            seg_start[pos] = lo;
+            pre[pos + k] = epre[(int64_t)k * gridDim.x + blockIdx.x] + re;
+        }
+        lo = hi;
+    }
+}
+
+__global__ void k_prb_sentinels(const int64_t *kbase, const uint32_t *kedges, int K, uint32_t *pre) {
+    for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < K; k += gridDim.x * blockDim.x)
+        pre[kbase[k + 1] + k] = kedges[k];
+}
+
+// Tile t of block k: first segment and segment count (searching the prefix).
+__global__ void k_prb_tiles(const uint32_t *pre, const int64_t *kbase, const uint32_t *kedges,
+                            const int64_t *tbase, int K, int2 *tiles) {
+    const int64_t total = tbase[K];
+    for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < total;
+         t += (int64_t)gridDim.x * blockDim.x) {
+        int k = 0;
+        while (tbase[k + 1] <= t) ++k;
+        const uint32_t *pk = pre + kbase[k] + k;
+        const int64_t nseg = kbase[k + 1] - kbase[k];
+        const uint64_t e0 = (uint64_t)(t - tbase[k]) * PR_TILE;
+        const uint64_t e1 = min((uint64_t)kedges[k], e0 + PR_TILE);
+        const int64_t j0 = upper_index(pk, nseg, (uint32_t)e0);
+        const int64_t j1 = upper_index(pk, nseg, (uint32_t)(e1 - 1));
+        tiles[t] = make_int2((int)j0, (int)min(j1 - j0 + 1, (int64_t)PR_TILE + 1));
+    }
+}
+
+struct PrbSmem {
+    uint32_t qe[PR_TILE + 2];
+    uint32_t st[PR_TILE + 1];
+    int32_t vv[PR_TILE + 1];
+    float acc[PR_TILE + 1];
+    uint16_t rid[PR_TILE];
+    int wmax[PR_BLOCK / 32];
+};
+
+// Pass k of an iteration: per tile of block k's segment edges, sum
+// c_in[col[e]] per segment (rows by scatter + max-scan, then all of a
+// thread's loads in flight), then add each segment's sum to its row's
+// accumulator.
+__global__ void __launch_bounds__(PR_BLOCK) k_prb_pass(const int32_t *__restrict__ col,
+                                                       const int32_t *__restrict__ seg_v,
+                                                       const uint32_t *__restrict__ seg_start,
+                                                       const uint32_t *__restrict__ pre, uint32_t E_k,
+                                                       const int2 *__restrict__ tiles,
+                                                       const float *__restrict__ c_in,
+                                                       float *__restrict__ acc_g) {
+    __shared__ PrbSmem sm;
+    const uint64_t e0 = (uint64_t)blockIdx.x * PR_TILE;
+    const uint64_t e1 = min((uint64_t)E_k, e0 + PR_TILE);
+    const int len = (int)(e1 - e0);
+    const int2 tr = __ldg(tiles + blockIdx.x);
+    const int64_t j0 = tr.x;
+    const int n = tr.y;
+    for (int j = threadIdx.x; j <= n; j += PR_BLOCK) {
+        sm.qe[j] = __ldg(pre + j0 + j);
+        if (j < n) {
+            sm.st[j] = __ldg(seg_start + j0 + j);
+            sm.vv[j] = __ldg(seg_v + j0 + j);
+            sm.acc[j] = 0.f;
+        }
+    }
+    __syncthreads();
+    int row[PR_ITEMS];
+    block_tile_rows(sm.rid, sm.wmax, sm.qe, (uint32_t)e0, n, len, row);
+    const int t0 = threadIdx.x * PR_ITEMS;
+    int32_t u[PR_ITEMS];
+#pragma unroll
+    for (int k = 0; k < PR_ITEMS; ++k) {
+        const uint32_t e = (uint32_t)(e0 + t0 + k);
+        u[k] = t0 + k < len ? __ldg(col + sm.st[row[k]] + (e - sm.qe[row[k]])) : -1;
+    }
+    float g[PR_ITEMS];
+#pragma unroll
+    for (int k = 0; k < PR_ITEMS; ++k) g[k] = u[k] >= 0 ? __ldg(c_in + u[k]) : 0.f;
+    add_runs(sm.acc, row, g, len - t0);
+    __syncthreads();
+    for (int j = threadIdx.x; j < n; j += PR_BLOCK)
+        if (sm.acc[j] != 0.f) atomicAdd(acc_g + sm.vv[j], sm.acc[j]);
+}
+
+// Ranks of the non-isolated vertices from the accumulated sums; clears them.
+__global__ void k_prb_finish(const int32_t *__restrict__ active, const uint32_t *__restrict__ aoff,
+                             int64_t n_active, float *__restrict__ acc_g, float *__restrict__ c_out,
+                             float *__restrict__ rank, float base, float d) {
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n_active;
+         i += (int64_t)gridDim.x * blockDim.x) {
+        const int32_t v = active[i];
+        const float r = base + d * acc_g[v];
+        acc_g[v] = 0.f;
+        c_out[v] = r / (float)(aoff[i + 1] - aoff[i]);
+        if (rank) rank[v] = r;
+    }
+}
+
+// Builds the column-blocked segments of g for blocks of 2^shift vertices.
+grx_status prb_build(grx_graph *g, int shift, cudaStream_t s) {
+    const int64_t B = 1ll << shift;
+    const int K = (int)((g->nv + B - 1) / B);
+    const int64_t nb = (g->n_active + PRB_BUILD - 1) / PRB_BUILD;
+    g->prb_K = 0;
+    if (K < 2 || K > GRX_PRB_MAX_K || nb == 0) return GRX_OK;
+    const size_t nkb = (size_t)K * (size_t)nb;
+    uint32_t *cnt = (uint32_t *)grx_ctx_alloc(g->ctx, nkb * 4, s);
+    uint32_t *es = (uint32_t *)grx_ctx_alloc(g->ctx, nkb * 4, s);
+    int64_t *dk = (int64_t *)grx_ctx_alloc(g->ctx, (size_t)(3 * K + 3) * 8, s);
+    if (!cnt || !es || !dk) return grx_fail(GRX_ENOMEM, "pagerank: column-block build allocation failed");
+    k_prb_count<<<(unsigned)nb, PRB_BUILD, (size_t)2 * K * 4, s>>>(g->col, g->aoff, g->n_active, shift, K,
+                                                                  cnt, es);
+    std::vector<uint32_t> hc(nkb), he(nkb);
+    GRX_CUDA(cudaMemcpyAsync(hc.data(), cnt, nkb * 4, cudaMemcpyDeviceToHost, s));
+    GRX_CUDA(cudaMemcpyAsync(he.data(), es, nkb * 4, cudaMemcpyDeviceToHost, s));
+    GRX_CUDA(cudaStreamSynchronize(s));
+    int64_t kbase[GRX_PRB_MAX_K + 1], tbase[GRX_PRB_MAX_K + 1];
+    uint32_t kedges[GRX_PRB_MAX_K];
+    kbase[0] = 0;
+    tbase[0] = 0;
+    for (int k = 0; k < K; ++k) {
+        uint64_t c = 0, e = 0;
+        for (int64_t b = 0; b < nb; ++b) {
+            const size_t x = (size_t)k * nb + b;
+            const uint32_t cc = hc[x], ee = he[x];
+            hc[x] = (uint32_t)c;
+            he[x] = (uint32_t)e;
+            c += cc;
+            e += ee;
+        }
+        kbase[k + 1] = kbase[k] + (int64_t)c;
+        kedges[k] = (uint32_t)e;
+        tbase[k + 1] = tbase[k] + (int64_t)((e + PR_TILE - 1) / PR_TILE);
+    }
+    const int64_t nseg = kbase[K];
+    int32_t *seg_v = (int32_t *)grx_alloc(g, (size_t)nseg * 4 + 16, s);
+    uint32_t *seg_start = (uint32_t *)grx_alloc(g, (size_t)nseg * 4 + 16, s);
+    uint32_t *pre = (uint32_t *)grx_alloc(g, (size_t)(nseg + K) * 4 + 16, s);
+    int2 *tiles = (int2 *)grx_alloc(g, (size_t)tbase[K] * 8 + 16, s);
+    if (!seg_v || !seg_start || !pre || !tiles)
+        return grx_fail(GRX_ENOMEM, "pagerank: column-block segment allocation failed");
+    std::vector<int64_t> hk((size_t)(3 * K + 3));
+    for (int k = 0; k <= K; ++k) {
+        hk[(size_t)k] = kbase[k];
+        hk[(size_t)(K + 1 + k)] = tbase[k];
+    }
+    for (int k = 0; k < K; ++k) hk[(size_t)(2 * K + 2 + k)] = kedges[k];
+    GRX_CUDA(cudaMemcpyAsync(cnt, hc.data(), nkb * 4, cudaMemcpyHostToDevice, s));
+    GRX_CUDA(cudaMemcpyAsync(es, he.data(), nkb * 4, cudaMemcpyHostToDevice, s));
+    GRX_CUDA(cudaMemcpyAsync(dk, hk.data(), hk.size() * 8, cudaMemcpyHostToDevice, s));
+    // kedges as uint32 for the kernels, packed after the int64 tables
+    uint32_t *dke = (uint32_t *)(dk + 2 * K + 2);
+    std::vector<uint32_t> hke(kedges, kedges + K);
+    GRX_CUDA(cudaMemcpyAsync(dke, hke.data(), (size_t)K * 4, cudaMemcpyHostToDevice, s));
+    k_prb_fill<<<(unsigned)nb, PRB_BUILD, 0, s>>>(g->col, g->active, g->aoff, g->n_active, shift, K, cnt, es,
+                                                  dk, seg_v, seg_start, pre);
+    k_prb_sentinels<<<1, 256, 0, s>>>(dk, dke, K, pre);
+    if (tbase[K] > 0) {
+        const int64_t blocks = (tbase[K] + 255) / 256 < 65536 ? (tbase[K] + 255) / 256 : 65536;
+        k_prb_tiles<<<(unsigned)blocks, 256, 0, s>>>(pre, dk, dke, dk + K + 1, K, tiles);
+    }
+    GRX_CUDA(cudaGetLastError());
+    GRX_CUDA(cudaStreamSynchronize(s));    // host tables above are locals
+    grx_ctx_free(g->ctx, cnt, nkb * 4, s);
+    grx_ctx_free(g->ctx, es, nkb * 4, s);
+    grx_ctx_free(g->ctx, dk, (size_t)(3 * K + 3) * 8, s);
+    g->prb_seg_v = seg_v;
+    g->prb_seg_start = seg_start;
+    g->prb_pre = pre;
+    g->prb_tiles = tiles;
+    for (int k = 0; k <= K; ++k) {
+        g->prb_kbase[k] = kbase[k];
+        g->prb_tbase[k] = tbase[k];
+    }
+    for (int k = 0; k < K; ++k) g->prb_kedges[k] = kedges[k];
+    g->prb_K = K;
+    g->prb_shift = shift;
+    return GRX_OK;
+}
+
 }  // namespace
 
 grx_status grx_pr_launch(grx_graph *g, float damping, int iters, float *rank, cudaStream_t s) {
@@ -131,6 +438,19 @@ grx_status grx_pr_launch(grx_graph *g, float damping, int iters, float *rank, cu
         if (!g->pr_c[0] || !g->pr_c[1] || !g->pr_s || !g->pr_fix)
             return grx_fail(GRX_ENOMEM, "pagerank: workspace allocation failed");
         GRX_CUDA(cudaMemsetAsync(g->pr_s, 0, (size_t)g->nv * 4, s));
+    }
+    // column blocks only when asked for: on GB300 at R-MAT scale 26 the
+    // unblocked gathers (22.5 ms per iteration) beat 2^21..2^25-vertex
+    // blocks (32..38 ms), the extra segment reads and reductions costing
+    // more than the DRAM sectors the L2-resident slices save
+    const int want = g->pr_shift_req > 0 ? g->pr_shift_req : -1;
+    bool blocked = false;
+    if (want > 0 && g->ne > 0 && ((int64_t)g->nv >> want) >= 1) {
+        if (!(g->prb_K >= 2 && g->prb_shift == want)) {
+            grx_status st = prb_build(g, want, s);
+            if (st != GRX_OK) return st;
+        }
+        blocked = g->prb_K >= 2 && g->prb_shift == want;
     }
     const double N = (double)g->nv;
     const double d = (double)damping;
@@ -156,7 +476,7 @@ grx_status grx_pr_launch(grx_graph *g, float damping, int iters, float *rank, cu
                                                                   (float)(1.0 / N), g->pr_c[0]);
     const int fix_blocks = (int)((ntiles + 255) / 256 > 0 ? (ntiles + 255) / 256 : 1);
     const int2 *tiles = nullptr;
-    if (ntiles > 0) {
+    if (ntiles > 0 && !blocked) {
         grx_status st = grx_edge_tiles(g, PR_TILE, s, &tiles);
         if (st != GRX_OK) return st;
     }
@@ -164,11 +484,24 @@ grx_status grx_pr_launch(grx_graph *g, float damping, int iters, float *rank, cu
         const float *c_in = g->pr_c[i & 1];
         float *c_out = g->pr_c[(i + 1) & 1];
         float *r_out = i == iters - 1 ? rank : nullptr;
-        k_pr_iter<<<(unsigned)ntiles, PR_BLOCK, 0, s>>>(g->col, g->active, g->aoff, tiles,
-                                                       g->ne, c_in, c_out, g->pr_s, g->pr_fix, r_out,
-                                                       base[(size_t)i], damping);
-        k_pr_fixup<<<fix_blocks, 256, 0, s>>>(g->pr_fix, ntiles, g->ro, g->off64, g->pr_s, c_out, r_out,
-                                              base[(size_t)i], damping);
+        if (blocked) {
+            for (int k = 0; k < g->prb_K; ++k) {
+                const int64_t nt = g->prb_tbase[k + 1] - g->prb_tbase[k];
+                if (nt == 0) continue;
+                const int64_t kb = g->prb_kbase[k];
+                k_prb_pass<<<(unsigned)nt, PR_BLOCK, 0, s>>>(g->col, g->prb_seg_v + kb, g->prb_seg_start + kb,
+                                                            g->prb_pre + kb + k, g->prb_kedges[k],
+                                                            g->prb_tiles + g->prb_tbase[k], c_in, g->pr_s);
+            }
+            k_prb_finish<<<init_blocks > 0 ? init_blocks : 1, 256, 0, s>>>(
+                g->active, g->aoff, g->n_active, g->pr_s, c_out, r_out, base[(size_t)i], damping);
+        } else {
+            k_pr_iter<<<(unsigned)ntiles, PR_BLOCK, 0, s>>>(g->col, g->active, g->aoff, tiles, g->ne, c_in,
+                                                           c_out, g->pr_s, g->pr_fix, r_out,
+                                                           base[(size_t)i], damping);
+            k_pr_fixup<<<fix_blocks, 256, 0, s>>>(g->pr_fix, ntiles, g->ro, g->off64, g->pr_s, c_out, r_out,
+                                                  base[(size_t)i], damping);
+        }
     }
     k_pr_fill<<<fill_blocks, 256, 0, s>>>(g->nz_bits, g->nv, (float)riso, 0, rank);
     GRX_CUDA(cudaGetLastError());

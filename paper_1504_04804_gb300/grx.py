@@ -76,6 +76,7 @@ SIGNATURES = [
     ("sssp", _I, [_P, ctypes.c_int32, _P, _P, _P]),
     ("cc", _I, [_P, _P, _P]),
     ("pagerank", _I, [_P, ctypes.c_float, _I, _P, _P]),
+    ("grx_pagerank_block", _I, [_P, _I]),
     ("grx_last_stats", _I, [_P, _P, _P]),
     ("bfs_multi", _I, [_P, _P, _I, _P, _P, _P]),
     ("sssp_multi", _I, [_P, _P, _I, _P, _P, _P]),
@@ -326,6 +327,12 @@ def pagerank(g: Graph, damping: float = 0.85, iters: int = 20, rank_out=None, st
     _check(lib().pagerank(g.handle, float(damping), int(iters), r.data_ptr(), _stream_ptr(stream)),
            "pagerank")
     return r
+
+
+def pagerank_block(g: Graph, shift: int):
+    """Column-block width (2^shift vertices) of pagerank's gathers; <= 0 =
+    no blocks (the default)."""
+    _check(lib().grx_pagerank_block(g.handle, int(shift)), "grx_pagerank_block")
 
 
 GRX_NOALLOC_MAX_NV = 1 << 19

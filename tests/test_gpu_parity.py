@@ -167,6 +167,29 @@ def test_pagerank_matches_oracle(grx, loaded, name):
         assert abs(r.sum() - 1.0) < 1e-4
 
 
+@pytest.mark.parametrize("name", list(GRAPHS))
+def test_pagerank_column_blocks_match_oracle(grx, loaded, name):
+    """Column-blocked gathers (forced small blocks: many passes per
+    iteration, rows split into many segments) within the same tolerance."""
+    g, dg = GRAPHS[name], loaded[name]
+    finest = max(1, int(np.ceil(np.log2(g.nv / 256))))      # at most 256 blocks
+    try:
+        for shift in sorted({finest, max(finest, int(np.log2(g.nv)) - 2)}):
+            if (g.nv >> shift) < 1:
+                continue
+            grx.pagerank_block(dg, shift)
+            for iters in (1, 20):
+                r = grx.pagerank(dg, 0.85, iters).cpu().numpy().astype(np.float64)
+                want = oracle.pagerank(g.row_offsets, g.col_indices, 0.85, iters)
+                rel = np.max(np.abs(r - want) / want)
+                assert rel <= PR_TOL, (name, shift, iters, rel)
+        if g.nv > 2 * 256:
+            with pytest.raises(grx.GrxError):
+                grx.pagerank_block(dg, 1)                     # too many blocks
+    finally:
+        grx.pagerank_block(dg, 0)
+
+
 def test_exhaustive_6_vertex_graphs_as_one_union(grx):
     """All 2^15 labelled graphs on 6 vertices as one disjoint union: CC over
     the union, BFS/SSSP from a vertex of a seeded sample of the graphs."""
