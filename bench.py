@@ -432,7 +432,7 @@ def main():
                          "launch_ms": sum(kern_ms) / len(kern_ms)},
             "cpu_baseline": cpu,
             "e2e": e2e,
-            "gpu_launches": 2 * len(order),
+            "gpu_launches": len(order),         # one persistent k_bfs_persistent per traversal
             "clocks": clocks,
             "detail": {"traversal_ms_median": statistics.median(step_ms),
                        "kernel_ms_median": statistics.median(kern_ms),

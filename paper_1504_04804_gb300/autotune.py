@@ -27,7 +27,7 @@ import time
 
 import numpy as np
 
-ALPHAS = (1e-4, 1e-3, 5e-3, 0.01, 0.05, 0.2)
+ALPHAS = (1e-6, 1e-5, 1e-4, 1e-3, 5e-3, 0.01, 0.05, 0.2)
 BETAS = (0.01, 0.1, 1.0)
 RULES = (0, 1)
 DEFAULT_CACHE = os.path.join(os.path.expanduser("~"), ".cache", "grx_autotune.json")
@@ -78,7 +78,7 @@ def _time_config(grx, torch, g, sources, kw, reps):
     return statistics.median(ts), sum(ts)
 
 
-def tune_bfs(g, row_offsets, n_sources: int = 4, seed: int = 2, reps: int = 2,
+def tune_bfs(g, row_offsets, n_sources: int = 8, seed: int = 2, reps: int = 2,
              cache: str | None = DEFAULT_CACHE, force: bool = False) -> dict:
     """Search the knobs for direction-optimising BFS on a loaded graph.
     Returns {"alpha", "beta", "exact_fv", "grid_blocks", "ms", "tried", "seconds",

@@ -58,6 +58,9 @@ namespace {
 #endif
 
 constexpr int BFS_BLOCK = 256;
+#ifndef GRX_BFS_MIN_BLOCKS
+#define GRX_BFS_MIN_BLOCKS 3                        // resident blocks per SM (register cap)
+#endif
 constexpr int WARPS = BFS_BLOCK / 32;
 constexpr int PUSH_ITEMS = GRX_PUSH_ITEMS;
 constexpr int WTILE = 32 * PUSH_ITEMS;              // edges per warp tile
@@ -65,7 +68,10 @@ constexpr int WTILE = 32 * PUSH_ITEMS;              // edges per warp tile
 #define GRX_PULL_LIGHT 2
 #endif
 constexpr int PULL_LIGHT = GRX_PULL_LIGHT;          // neighbours probed per vertex first (1 or 2)
-constexpr int PULL_PER_LANE = 4;
+#ifndef GRX_PULL_PER_LANE
+#define GRX_PULL_PER_LANE 4
+#endif
+constexpr int PULL_PER_LANE = GRX_PULL_PER_LANE;    // candidates per lane per round
 constexpr int PULL_WCH = 32 * PULL_PER_LANE;        // candidates per warp round
 constexpr int PULL_HITEMS = PUSH_ITEMS;             // heavy-phase edges per lane per step
 constexpr int PULL_HSTEP = 32 * PULL_HITEMS;        // heavy-phase edges per warp step
@@ -781,7 +787,7 @@ __device__ void init_phase(const BfsArgs<OffT> &a, const LevelState &st0) {
 }
 
 template <typename OffT, bool PARENT, bool STATS>
-__global__ void __launch_bounds__(BFS_BLOCK, 3) k_bfs_persistent(BfsArgs<OffT> a) {
+__global__ void __launch_bounds__(BFS_BLOCK, GRX_BFS_MIN_BLOCKS) k_bfs_persistent(BfsArgs<OffT> a) {
     __shared__ LevelState s_st;
     __shared__ WarpSmem<OffT> wsm[WARPS];
     WarpSmem<OffT> &w = wsm[threadIdx.x >> 5];
