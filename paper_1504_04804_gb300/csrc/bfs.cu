@@ -76,6 +76,7 @@ constexpr int PULL_WCH = 32 * PULL_PER_LANE;        // candidates per warp round
 constexpr int PULL_HITEMS = PUSH_ITEMS;             // heavy-phase edges per lane per step
 constexpr int PULL_HSTEP = 32 * PULL_HITEMS;        // heavy-phase edges per warp step
 constexpr int SC_VERTS = 32 * 32;                   // vertices of a 32-word chunk
+static_assert(WTILE == 256 && PULL_HSTEP == 256, "warp_tile_rows8 covers 256-position tiles");
 
 enum { DIR_PUSH = 0, DIR_PULL = 1 };
 enum { OP_QPUSH, OP_BMARK, OP_BFINAL, OP_COMPACT, OP_PULL };
@@ -234,46 +235,6 @@ __device__ LevelState next_state(const BfsArgs<OffT> &a, const LevelState &st, b
     return ns;
 }
 
-// Row of every position of a warp tile, without per-item searches or loops
-// (branches are the scarce resource of a hot tile loop): positions start at
-// row 0; each non-empty row j > 0 that starts inside the tile writes j at its
-// start; an inclusive max-scan over the positions then gives every position
-// its row.  rid holds WTILE entries, PUSH_ITEMS consecutive ones per lane;
-// starts[0..n] are the rows' first positions (non-decreasing, starts[n] =
-// end of row n-1).  On return row[k] is the row of position
-// lane*PUSH_ITEMS + k (meaningful where the position lies inside a row).
-__device__ __forceinline__ void tile_rows(uint16_t *rid, const uint32_t *starts, uint32_t origin,
-                                          int n, int (&row)[PUSH_ITEMS]) {
-    const unsigned int lane = threadIdx.x & 31;
-    static_assert(PUSH_ITEMS == 8, "tile_rows moves 8 entries per lane as one 16-byte word");
-    reinterpret_cast<uint4 *>(rid)[lane] = make_uint4(0u, 0u, 0u, 0u);
-    __syncwarp();
-    for (int j = 1 + (int)lane; j < n; j += 32) {
-        const uint32_t p = starts[j] - origin;
-        if (p < (uint32_t)WTILE && starts[j + 1] > starts[j]) rid[p] = (uint16_t)j;
-    }
-    __syncwarp();
-    const uint4 q4 = reinterpret_cast<const uint4 *>(rid)[lane];
-    const uint32_t pk[4] = {q4.x, q4.y, q4.z, q4.w};
-    int m = 0;
-#pragma unroll
-    for (int k = 0; k < PUSH_ITEMS; ++k) {
-        m = max(m, (int)((pk[k >> 1] >> ((k & 1) * 16)) & 0xffffu));
-        row[k] = m;
-    }
-    int x = m;                                   // inclusive max-scan of the lanes' maxima
-#pragma unroll
-    for (int o = 1; o < 32; o <<= 1) {
-        const int y = __shfl_up_sync(GRX_FULL_MASK, x, o);
-        if (lane >= (unsigned)o) x = max(x, y);
-    }
-    int carry = __shfl_up_sync(GRX_FULL_MASK, x, 1);
-    if (lane == 0) carry = 0;
-#pragma unroll
-    for (int k = 0; k < PUSH_ITEMS; ++k) row[k] = max(row[k], carry);
-    __syncwarp();
-}
-
 // Loads warp tile `tile` of the frontier's edge sequence: the frontier
 // elements that start before the tile's end go to shared memory (i0 = the
 // element holding the tile's first edge), then every lane takes PUSH_ITEMS
@@ -313,7 +274,7 @@ __device__ __forceinline__ int64_t push_tile(const BfsArgs<OffT> &a, const int32
     __syncwarp();
     const uint32_t next_start = w.qe[n];
     int row[PUSH_ITEMS];
-    tile_rows(w.rid, w.qe, (uint32_t)e0, n, row);
+    warp_tile_rows8(w.rid, w.qe, (uint32_t)e0, n, row);
     const uint32_t t0 = (uint32_t)e0 + lane * PUSH_ITEMS;
     valid = 0;
 #pragma unroll
@@ -642,7 +603,7 @@ __device__ void pull_level(const BfsArgs<OffT> &a, const LevelState &st, PullWar
                 __syncwarp();
                 const uint32_t steplen = min(total, (uint32_t)PULL_HSTEP);
                 int hrow[PULL_HITEMS];
-                tile_rows(w.hrid, w.hofs, 0u, nh, hrow);
+                warp_tile_rows8(w.hrid, w.hofs, 0u, nh, hrow);
                 const uint32_t j0 = lane * PULL_HITEMS;
                 int32_t uu[PULL_HITEMS];
 #pragma unroll

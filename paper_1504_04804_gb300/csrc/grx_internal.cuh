@@ -517,6 +517,45 @@ __device__ __forceinline__ int warp_compact_bits(uint32_t bits, uint16_t *list) 
     return total;
 }
 
+// Row of every position of a warp tile, without per-item searches or loops
+// (branches are the scarce resource of a hot tile loop): positions start at
+// row 0; each non-empty row j > 0 that starts inside the tile writes j at its
+// start; an inclusive max-scan over the positions then gives every position
+// its row.  rid (16-byte aligned) holds 256 entries, 8 consecutive ones per lane;
+// starts[0..n] are the rows' first positions (non-decreasing, starts[n] =
+// end of row n-1).  On return row[k] is the row of position
+// lane*8 + k (meaningful where the position lies inside a row).
+__device__ __forceinline__ void warp_tile_rows8(uint16_t *rid, const uint32_t *starts, uint32_t origin,
+                                                int n, int (&row)[8]) {
+    const unsigned int lane = threadIdx.x & 31;
+    reinterpret_cast<uint4 *>(rid)[lane] = make_uint4(0u, 0u, 0u, 0u);
+    __syncwarp();
+    for (int j = 1 + (int)lane; j < n; j += 32) {
+        const uint32_t p = starts[j] - origin;
+        if (p < 256u && starts[j + 1] > starts[j]) rid[p] = (uint16_t)j;
+    }
+    __syncwarp();
+    const uint4 q4 = reinterpret_cast<const uint4 *>(rid)[lane];
+    const uint32_t pk[4] = {q4.x, q4.y, q4.z, q4.w};
+    int m = 0;
+#pragma unroll
+    for (int k = 0; k < 8; ++k) {
+        m = max(m, (int)((pk[k >> 1] >> ((k & 1) * 16)) & 0xffffu));
+        row[k] = m;
+    }
+    int x = m;                                   // inclusive max-scan of the lanes' maxima
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const int y = __shfl_up_sync(GRX_FULL_MASK, x, o);
+        if (lane >= (unsigned)o) x = max(x, y);
+    }
+    int carry = __shfl_up_sync(GRX_FULL_MASK, x, 1);
+    if (lane == 0) carry = 0;
+#pragma unroll
+    for (int k = 0; k < 8; ++k) row[k] = max(row[k], carry);
+    __syncwarp();
+}
+
 template <typename T>
 __device__ __forceinline__ T warp_sum(T x) {
 #pragma unroll

@@ -1,218 +1,311 @@
 // SSSP (Table 1): frontier label-correcting relaxation.  Each round advances
 // the vertices whose distance improved in the previous round: for every edge
-// (u, v, w) it proposes dist[u] + w with atomicMin -- the min combiner the
-// paper uses for SSSP labels (Sec. 3) -- and queues v at most once per round
-// (a per-vertex round stamp is the filter).  Rounds repeat until no distance
-// improves; the result is the exact shortest-path distance.
+// (u, v, w) it proposes dist[u] + w with an atomic min -- the min combiner the
+// paper uses for SSSP labels (Sec. 3) -- and v joins the next frontier once.
+// Rounds repeat until no distance improves; the result is the exact
+// shortest-path distance.
 //
-// Same persistent, load-balanced structure as the push step of BFS: the
-// frontier's edges are cut into equal tiles using the degree prefix that the
-// append atomic produced, each thread keeps a run of SS_ITEMS edges' loads and
-// atomics in flight, and rounds are separated by a bounded grid barrier.
+// Same persistent, load-balanced structure as the push step of BFS: a frontier
+// queue slot carries the vertex, its row start and the exclusive prefix of the
+// frontier's degrees, so the frontier's edges are cut into equal warp tiles
+// (each warp a contiguous range, rows by a branch-free scatter + max-scan) and
+// each lane keeps a run of 8 edges' loads in flight.  Two kinds of rounds:
+//  * small rounds: an improving lane claims v with the atomic min's old value,
+//    a per-vertex round stamp keeps v once, and v is appended with one
+//    warp-aggregated atomic;
+//  * rounds with at least push_bitmap * V edges: the atomic min is a
+//    reduction (no value returned) and v's bit is OR-ed into a changed bitmap;
+//    a second phase, by warps owning 32-word chunks of the bitmap, appends the
+//    changed vertices in vertex order and clears the bitmap.  A lane reduces
+//    only when its proposal beats the current distance read from L2, so every
+//    marked vertex did improve in the round and every improvement is marked.
+// Rounds and phases are separated by the bounded grid barrier.
 #include "grx_internal.cuh"
 
 namespace {
 
 constexpr int SS_BLOCK = 256;
+constexpr int SS_WARPS = SS_BLOCK / 32;
 constexpr int SS_ITEMS = 8;
-constexpr int SS_TILE = SS_BLOCK * SS_ITEMS;
+constexpr int SS_WTILE = 32 * SS_ITEMS;
+constexpr int SS_RPL = 4;                    // finalize: vertices per lane per round
 
 template <typename OffT>
 struct SsspArgs {
     int32_t nv;
+    int64_t words;
     const OffT *ro;
     const int32_t *col;
     const uint32_t *w;
     uint32_t *dist;
     int32_t *stamp;
+    uint32_t *cbits;                         // changed bitmap of reduction rounds
     int32_t *Q[3];
     uint32_t *E[3];
+    OffT *R[3];
     TravCtl *ctl;
     unsigned int *bar_flags;
     DevStats *stats;
+    uint32_t bmp_min_T;
     unsigned long long timeout_ns;
     int32_t src;
 };
 
-template <typename OffT>
-struct SsspSmem {
-    uint32_t qe[SS_TILE + 1];
-    int32_t u[SS_TILE + 1];
-    OffT rs[SS_TILE + 1];
-    uint32_t du[SS_TILE + 1];
-    int64_t i0;
-    int n;
-    uint32_t q, T;
+struct SsState {
+    int L;
+    int phase;
+    int bmp;
     int done;
+    uint32_t q, T;
 };
 
-template <typename OffT, bool STATS>
-__device__ void relax_round(const SsspArgs<OffT> &a, int L, uint32_t q, uint64_t T,
-                            SsspSmem<OffT> &sm) {
+template <typename OffT>
+union SsWarpSmem {
+    struct {
+        uint32_t qe[SS_WTILE + 2];
+        int32_t u[SS_WTILE + 1];
+        OffT rs[SS_WTILE + 1];
+        uint32_t du[SS_WTILE + 1];
+        alignas(16) uint16_t rid[SS_WTILE];
+    };
+    uint16_t list[32 * 32];
+};
+
+template <typename OffT>
+__device__ __forceinline__ void ss_set_kind(const SsspArgs<OffT> &a, SsState &s) {
+    s.bmp = s.T >= a.bmp_min_T;
+}
+
+// Phase 0 of round L: relax the edges of Q_L.
+template <typename OffT, bool BMP>
+__device__ void relax_round(const SsspArgs<OffT> &a, const SsState &st, SsWarpSmem<OffT> &w) {
+    const int L = st.L;
+    const unsigned int lane = threadIdx.x & 31;
     const int32_t *Qv = pick3(a.Q[0], a.Q[1], a.Q[2], L % 3);
     const uint32_t *Qe = pick3(a.E[0], a.E[1], a.E[2], L % 3);
+    const OffT *Qr = pick3(a.R[0], a.R[1], a.R[2], L % 3);
     int32_t *Qv_out = pick3(a.Q[0], a.Q[1], a.Q[2], (L + 1) % 3);
     uint32_t *Qe_out = pick3(a.E[0], a.E[1], a.E[2], (L + 1) % 3);
+    OffT *Qr_out = pick3(a.R[0], a.R[1], a.R[2], (L + 1) % 3);
     unsigned long long *ctr = &a.ctl->qpack[(L + 1) & 3];
-    const uint64_t ntiles = (T + SS_TILE - 1) / SS_TILE;
-    for (uint64_t tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
-        const uint64_t e0 = tile * SS_TILE;
-        const uint64_t e1 = min(T, e0 + SS_TILE);
-        if (threadIdx.x == 0) {
-            int64_t i0 = upper_index_cg(Qe, q, (uint32_t)e0);
-            int64_t i1 = upper_index_cg(Qe, q, (uint32_t)(e1 - 1));
-            int n = (int)(i1 - i0 + 1);
-            if (n > SS_TILE + 1) {
-                grx_set_status(a.ctl, GRX_EINVAL);
-                n = SS_TILE + 1;
+    const int64_t q = st.q;
+    const uint64_t T = st.T;
+    const uint64_t ntiles = (T + SS_WTILE - 1) / SS_WTILE;
+    const uint64_t nwarps = (uint64_t)gridDim.x * SS_WARPS;
+    const uint64_t gw = (uint64_t)blockIdx.x * SS_WARPS + (threadIdx.x >> 5);
+    const uint64_t per = (ntiles + nwarps - 1) / nwarps;
+    const uint64_t tb0 = gw * per;
+    const uint64_t tb1 = min(ntiles, tb0 + per);
+    if (tb0 >= tb1) return;
+    int64_t i0 = warp_upper_index_cg(Qe, q, (uint32_t)(tb0 * SS_WTILE));
+    for (uint64_t tile = tb0; tile < tb1; ++tile) {
+        const uint64_t e0 = tile * SS_WTILE;
+        const uint32_t e1 = (uint32_t)min(T, e0 + SS_WTILE);
+        // frontier elements starting before e1, 32 per round
+        int n = 0;
+        for (;;) {
+            const int64_t idx = i0 + n + lane;
+            uint32_t qe = 0xffffffffu;
+            if (idx < q) qe = __ldcg(Qe + idx);
+            const bool in = idx < q && qe < e1;
+            if (n + (int)lane <= SS_WTILE + 1) w.qe[n + lane] = qe;
+            if (in && n + (int)lane <= SS_WTILE) {
+                const int32_t u = __ldcg(Qv + idx);
+                w.u[n + lane] = u;
+                w.rs[n + lane] = __ldcg(Qr + idx);
+                w.du[n + lane] = __ldcg(a.dist + u);
             }
-            sm.i0 = i0;
-            sm.n = n;
+            const int cnt = __popc(__ballot_sync(GRX_FULL_MASK, in));
+            n += cnt;
+            if (cnt < 32) break;
+            if (n > SS_WTILE) {              // only possible with a malformed graph
+                if (lane == 0) grx_set_status(a.ctl, GRX_EINVAL);
+                n = SS_WTILE;
+                break;
+            }
         }
-        __syncthreads();
-        const int64_t i0 = sm.i0;
-        const int n = sm.n;
-        for (int j = threadIdx.x; j < n; j += SS_BLOCK) {
-            int32_t u = __ldcg(Qv + i0 + j);
-            sm.qe[j] = __ldcg(Qe + i0 + j);
-            sm.u[j] = u;
-            sm.rs[j] = __ldg(a.ro + u);
-            sm.du[j] = __ldcg(a.dist + u);
-        }
-        __syncthreads();
-        // a run of SS_ITEMS consecutive edges per thread, all loads in flight together
-        const uint64_t t0 = e0 + (uint64_t)threadIdx.x * SS_ITEMS;
+        __syncwarp();
+        const uint32_t next_start = w.qe[n];
+        int row[SS_ITEMS];
+        warp_tile_rows8(w.rid, w.qe, (uint32_t)e0, n, row);
+        const uint32_t t0 = (uint32_t)e0 + lane * SS_ITEMS;
         int32_t v[SS_ITEMS];
-        uint32_t nd[SS_ITEMS];
-        uint32_t valid = 0;
+        uint32_t wt[SS_ITEMS], du[SS_ITEMS];
 #pragma unroll
         for (int k = 0; k < SS_ITEMS; ++k) {
-            v[k] = 0;
+            const uint32_t e = t0 + k;
+            const int j = row[k];
+            const bool ok = e < e1;
+            const OffT idx = ok ? w.rs[j] + (OffT)(e - w.qe[j]) : (OffT)0;
+            v[k] = ok ? __ldg(a.col + idx) : -1;
+            wt[k] = ok ? __ldg(a.w + idx) : 0u;
+            du[k] = ok ? w.du[j] : 0xffffffffu;
+        }
+        __syncwarp();
+        uint32_t nd[SS_ITEMS], cur[SS_ITEMS];
+#pragma unroll
+        for (int k = 0; k < SS_ITEMS; ++k) {
             nd[k] = 0xffffffffu;
+            if (v[k] >= 0 && du[k] != 0xffffffffu) {
+                const uint64_t s64 = (uint64_t)du[k] + wt[k];
+                if (s64 >= 0xffffffffull) grx_set_status(a.ctl, GRX_ERANGE);
+                else nd[k] = (uint32_t)s64;
+            }
+            cur[k] = nd[k] != 0xffffffffu ? __ldcg(a.dist + v[k]) : 0u;
         }
-        if (t0 < e1) {
-            int j = upper_index_smem(sm.qe, n, (uint32_t)t0);
-            uint32_t wt[SS_ITEMS];
-            uint32_t du[SS_ITEMS];
+        if (BMP) {
 #pragma unroll
             for (int k = 0; k < SS_ITEMS; ++k) {
-                const uint64_t e = t0 + k;
-                wt[k] = 0;
-                du[k] = 0xffffffffu;
-                if (e < e1) {
-                    while (j + 1 < n && sm.qe[j + 1] <= (uint32_t)e) ++j;
-                    const OffT idx = sm.rs[j] + (OffT)((uint32_t)e - sm.qe[j]);
-                    v[k] = __ldg(a.col + idx);
-                    wt[k] = __ldg(a.w + idx);
-                    du[k] = sm.du[j];
-                    valid |= 1u << k;
+                if (nd[k] < cur[k]) {
+                    atomicMin(a.dist + v[k], nd[k]);                     // results unused: reductions
+                    atomicOr(a.cbits + (v[k] >> 5), 1u << (v[k] & 31));
                 }
             }
+        } else {
+            uint32_t improved = 0;
 #pragma unroll
             for (int k = 0; k < SS_ITEMS; ++k) {
-                if (valid >> k & 1u) {
-                    const uint64_t s64 = (uint64_t)du[k] + wt[k];
-                    if (s64 >= 0xffffffffull) {
-                        grx_set_status(a.ctl, GRX_ERANGE);
-                        valid &= ~(1u << k);
-                    } else {
-                        nd[k] = (uint32_t)s64;
-                    }
+                if (nd[k] < cur[k]) {
+                    const uint32_t old = atomicMin(a.dist + v[k], nd[k]);
+                    if (nd[k] < old) improved |= 1u << k;
                 }
             }
-        }
-        uint32_t cur[SS_ITEMS];
+            uint32_t queued = 0;
 #pragma unroll
-        for (int k = 0; k < SS_ITEMS; ++k) cur[k] = (valid >> k & 1u) ? __ldcg(a.dist + v[k]) : 0u;
-        uint32_t improved = 0;
+            for (int k = 0; k < SS_ITEMS; ++k)
+                if ((improved >> k & 1u) && atomicExch(a.stamp + v[k], L + 1) != L + 1) queued |= 1u << k;
+            uint32_t deg[SS_ITEMS];
+            OffT rb[SS_ITEMS];
+            uint32_t app = 0;
 #pragma unroll
-        for (int k = 0; k < SS_ITEMS; ++k) {
-            if ((valid >> k & 1u) && nd[k] < cur[k]) {
-                const uint32_t old = atomicMin(a.dist + v[k], nd[k]);
-                if (nd[k] < old) improved |= 1u << k;
+            for (int k = 0; k < SS_ITEMS; ++k) {
+                rb[k] = 0;
+                deg[k] = 0;
+                if (queued >> k & 1u) {
+                    rb[k] = __ldg(a.ro + v[k]);
+                    deg[k] = (uint32_t)(__ldg(a.ro + v[k] + 1) - rb[k]);
+                    if (deg[k]) app |= 1u << k;
+                }
             }
+            warp_append_items<SS_ITEMS, OffT>(v, deg, rb, app, Qv_out, Qe_out, Qr_out, ctr);
         }
-        uint32_t queued = 0;
-#pragma unroll
-        for (int k = 0; k < SS_ITEMS; ++k)
-            if ((improved >> k & 1u) && atomicExch(a.stamp + v[k], L + 1) != L + 1) queued |= 1u << k;
-        uint32_t deg[SS_ITEMS];
-        OffT rb[SS_ITEMS], re[SS_ITEMS];
-#pragma unroll
-        for (int k = 0; k < SS_ITEMS; ++k) {
-            rb[k] = 0;
-            re[k] = 0;
-            if (queued >> k & 1u) {
-                rb[k] = __ldg(a.ro + v[k]);
-                re[k] = __ldg(a.ro + v[k] + 1);
-            }
-        }
-        uint32_t app = 0;
-#pragma unroll
-        for (int k = 0; k < SS_ITEMS; ++k) {
-            deg[k] = (uint32_t)(re[k] - rb[k]);
-            if ((queued >> k & 1u) && deg[k]) app |= 1u << k;
-        }
-        warp_append_items<SS_ITEMS, OffT>(v, deg, rb, app, Qv_out, Qe_out, (OffT *)nullptr, ctr);
-        __syncthreads();
+        i0 = (next_start == e1) ? i0 + n : i0 + n - 1;
+        __syncwarp();
     }
-    if (STATS && blockIdx.x == 0 && threadIdx.x == 0 && L < GRX_MAX_LEVELS_STATS) {
-        a.stats->dir[L] = 0;
-        a.stats->frontier[L] = q;
-        a.stats->edges_examined[L] = T;
-        a.stats->vertices_scanned[L] = q;
-        a.stats->levels = L + 1;
+}
+
+// Phase 1 of a reduction round: the changed bitmap's vertices (with edges)
+// become Q_{L+1} in vertex order; the bitmap is cleared.
+template <typename OffT>
+__device__ void changed_to_queue(const SsspArgs<OffT> &a, const SsState &st, uint16_t *list) {
+    const int L = st.L;
+    int32_t *Qv_out = pick3(a.Q[0], a.Q[1], a.Q[2], (L + 1) % 3);
+    uint32_t *Qe_out = pick3(a.E[0], a.E[1], a.E[2], (L + 1) % 3);
+    OffT *Qr_out = pick3(a.R[0], a.R[1], a.R[2], (L + 1) % 3);
+    unsigned long long *ctr = &a.ctl->qpack[(L + 1) & 3];
+    const unsigned int lane = threadIdx.x & 31;
+    const int64_t nsc = (a.words + 31) / 32;
+    const int64_t nwarps = (int64_t)gridDim.x * SS_WARPS;
+    for (int64_t sc = (int64_t)blockIdx.x * SS_WARPS + (threadIdx.x >> 5); sc < nsc; sc += nwarps) {
+        const int64_t wd = sc * 32 + lane;
+        const uint32_t bits = wd < a.words ? __ldcg(a.cbits + wd) : 0u;
+        if (bits) a.cbits[wd] = 0u;
+        const int n = warp_compact_bits(bits, list);
+        for (int base = 0; base < n; base += 32 * SS_RPL) {
+            int32_t v[SS_RPL];
+            uint32_t deg[SS_RPL];
+            OffT rb[SS_RPL];
+            uint32_t app = 0;
+#pragma unroll
+            for (int k = 0; k < SS_RPL; ++k) {
+                const int i = base + k * 32 + (int)lane;
+                v[k] = i < n ? (int32_t)(sc * 1024 + list[i]) : 0;
+                rb[k] = 0;
+                deg[k] = 0;
+                if (i < n) {
+                    rb[k] = __ldg(a.ro + v[k]);
+                    deg[k] = (uint32_t)(__ldg(a.ro + v[k] + 1) - rb[k]);
+                    if (deg[k]) app |= 1u << k;
+                }
+            }
+            warp_append_items<SS_RPL, OffT>(v, deg, rb, app, Qv_out, Qe_out, Qr_out, ctr);
+        }
+        __syncwarp();
     }
 }
 
 template <typename OffT, bool STATS>
-__global__ void __launch_bounds__(SS_BLOCK) k_sssp_persistent(SsspArgs<OffT> a) {
-    __shared__ SsspSmem<OffT> sm;
+__global__ void __launch_bounds__(SS_BLOCK, 3) k_sssp_persistent(SsspArgs<OffT> a) {
+    __shared__ SsState s_st;
+    __shared__ SsWarpSmem<OffT> wsm[SS_WARPS];
+    SsWarpSmem<OffT> &w = wsm[threadIdx.x >> 5];
     FlagBarrier bar{a.bar_flags, &a.ctl->bar_release, a.ctl, a.timeout_ns, 0u};
     if (threadIdx.x == 0) {
-        uint32_t deg = (uint32_t)(a.ro[a.src + 1] - a.ro[a.src]);
-        sm.q = deg ? 1u : 0u;
-        sm.T = deg;
-        sm.done = deg == 0;
+        SsState s;
+        const uint32_t deg = (uint32_t)(a.ro[a.src + 1] - a.ro[a.src]);
+        s.L = 0;
+        s.phase = 0;
+        s.q = deg ? 1u : 0u;
+        s.T = deg;
+        s.done = deg == 0;
+        ss_set_kind(a, s);
+        s_st = s;
     }
     __syncthreads();
-    int L = 0;
-    for (;; ++L) {
-        const uint32_t q = sm.q;
-        const uint32_t T = sm.T;
-        if (sm.done) break;
-        if (blockIdx.x == 0 && threadIdx.x == 0) {
+    for (;;) {
+        const SsState st = s_st;
+        if (st.done) break;
+        const int L = st.L;
+        if (st.phase == 0 && blockIdx.x == 0 && threadIdx.x == 0) {
             a.ctl->qpack[(L + 2) & 3] = 0ull;
-            if (STATS && L < GRX_MAX_LEVELS_STATS) a.stats->level_t0[L] = grx_globaltimer();
+            if (STATS && L < GRX_MAX_LEVELS_STATS) {
+                a.stats->level_t0[L] = grx_globaltimer();
+                a.stats->dir[L] = 0;
+                a.stats->frontier[L] = st.q;
+                a.stats->edges_examined[L] = st.T;
+                a.stats->vertices_scanned[L] = st.q;
+                a.stats->levels = L + 1;
+            }
         }
-        relax_round<OffT, STATS>(a, L, q, T, sm);
+        if (st.phase == 1) changed_to_queue<OffT>(a, st, w.list);
+        else if (st.bmp) relax_round<OffT, true>(a, st, w);
+        else relax_round<OffT, false>(a, st, w);
         if (!flag_barrier(bar)) return;
         if (threadIdx.x == 0) {
-            unsigned long long pk = ld_relaxed_u64(&a.ctl->qpack[(L + 1) & 3]);
-            sm.q = (uint32_t)(pk >> 32);
-            sm.T = (uint32_t)pk;
-            sm.done = sm.q == 0;
-            if (STATS && blockIdx.x == 0 && L < GRX_MAX_LEVELS_STATS) a.stats->discovered[L] = sm.q;
+            SsState ns = st;
+            if (st.bmp && st.phase == 0) {
+                ns.phase = 1;
+            } else {
+                const unsigned long long pk = ld_relaxed_u64(&a.ctl->qpack[(L + 1) & 3]);
+                ns.L = L + 1;
+                ns.phase = 0;
+                ns.q = (uint32_t)(pk >> 32);
+                ns.T = (uint32_t)pk;
+                ns.done = ns.q == 0;
+                ss_set_kind(a, ns);
+                if (STATS && blockIdx.x == 0 && L < GRX_MAX_LEVELS_STATS) a.stats->discovered[L] = ns.q;
+            }
+            s_st = ns;
         }
         __syncthreads();
     }
     if (blockIdx.x == 0 && threadIdx.x == 0) {
-        a.ctl->levels_run = L;
-        if (STATS && L <= GRX_MAX_LEVELS_STATS) a.stats->level_t0[L] = grx_globaltimer();
+        a.ctl->levels_run = s_st.L;
+        if (STATS && s_st.L <= GRX_MAX_LEVELS_STATS) a.stats->level_t0[s_st.L] = grx_globaltimer();
     }
 }
 
-__global__ void k_sssp_init(int32_t src, const void *ro, int off64, uint32_t *dist, int32_t *Q0,
-                            uint32_t *E0, TravCtl *ctl, DevStats *stats, int stats_on) {
-    int64_t b = off64 ? ((const int64_t *)ro)[src] : ((const int32_t *)ro)[src];
-    int64_t e = off64 ? ((const int64_t *)ro)[src + 1] : ((const int32_t *)ro)[src + 1];
-    uint32_t deg = (uint32_t)(e - b);
+template <typename OffT>
+__global__ void k_sssp_init(int32_t src, const OffT *ro, uint32_t *dist, int32_t *Q0, uint32_t *E0, OffT *R0,
+                            TravCtl *ctl, DevStats *stats, int stats_on) {
+    const OffT b = ro[src];
+    const uint32_t deg = (uint32_t)(ro[src + 1] - b);
     dist[src] = 0;
     Q0[0] = src;
     E0[0] = 0;
+    R0[0] = b;
     ctl->qpack[0] = deg ? ((1ull << 32) | deg) : 0ull;
     for (int i = 1; i < 4; ++i) ctl->qpack[i] = 0ull;
-    ctl->bar_count = 0u;
     if (stats_on) stats->levels = 0;
 }
 
@@ -221,20 +314,31 @@ grx_status launch_typed(grx_graph *g, int32_t src, uint32_t *dist, const grx_opt
                         cudaStream_t s) {
     SsspArgs<OffT> a;
     a.nv = g->nv;
+    a.words = g->words;
     a.ro = (const OffT *)g->ro;
     a.col = g->col;
     a.w = g->w;
     a.dist = dist;
     a.stamp = g->stamp;
+    a.cbits = g->fbits[0];
     for (int i = 0; i < 3; ++i) {
         a.Q[i] = g->qv[i];
         a.E[i] = g->qe[i];
+        a.R[i] = (OffT *)g->qr[i];
     }
     a.ctl = g->ctl;
     a.bar_flags = g->bar_flags;
     a.stats = g->stats;
     a.timeout_ns = grx_timeout_ns(o);
     a.src = src;
+    {   // reduction rounds when a round's edges reach push_bitmap * nv (0 = 1/8, < 0 = never)
+        const double pb = o->push_bitmap == 0.f ? 0.125 : (double)o->push_bitmap;
+        const double t = pb * (double)g->nv;
+        a.bmp_min_T = pb < 0 ? 0xffffffffu : (t < 1.0 ? 1u : (t > 4294967295.0 ? 0xffffffffu : (uint32_t)t));
+    }
+    k_sssp_init<OffT><<<1, 1, 0, s>>>(src, a.ro, dist, g->qv[0], g->qe[0], a.R[0], g->ctl, g->stats,
+                                      o->collect_stats);
+    GRX_CUDA(cudaGetLastError());
     static int per_sm = -1;
     if (per_sm < 0) {
         GRX_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_sssp_persistent<OffT, STATS>,
@@ -261,10 +365,8 @@ grx_status grx_sssp_launch(grx_graph *g, int32_t src, uint32_t *dist, const grx_
     const size_t nv = (size_t)g->nv;
     GRX_CUDA(cudaMemsetAsync(dist, 0xff, nv * 4, s));
     GRX_CUDA(cudaMemsetAsync(g->stamp, 0, nv * 4, s));
+    GRX_CUDA(cudaMemsetAsync(g->fbits[0], 0, (size_t)g->words * 4, s));
     if (o->collect_stats) GRX_CUDA(cudaMemsetAsync(g->stats, 0, sizeof(DevStats), s));
-    k_sssp_init<<<1, 1, 0, s>>>(src, g->ro, g->off64, dist, g->qv[0], g->qe[0], g->ctl, g->stats,
-                                o->collect_stats);
-    GRX_CUDA(cudaGetLastError());
     if (g->off64)
         return o->collect_stats ? launch_typed<int64_t, true>(g, src, dist, o, s)
                                 : launch_typed<int64_t, false>(g, src, dist, o, s);

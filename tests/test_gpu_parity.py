@@ -138,14 +138,16 @@ def test_bfs_small_grids(grx, loaded):
 
 
 @pytest.mark.parametrize("name", list(GRAPHS))
-def test_sssp_matches_oracle(grx, loaded, name):
+@pytest.mark.parametrize("pb", list(PUSH_BITMAP))
+def test_sssp_matches_oracle(grx, loaded, name, pb):
     g, dg = GRAPHS[name], loaded[name]
+    o = grx.opts(push_bitmap=PUSH_BITMAP[pb])
     for s in _sources(g, 3) + [g.nv - 1]:
-        d = grx.sssp(dg, s)
+        d = grx.sssp(dg, s, opts=o)
         grx.graph_status(dg)
         got = grx.as_uint32(d)
         want = oracle.sssp(g.row_offsets, g.col_indices, g.weights, s)
-        assert np.array_equal(got, want), (name, s)
+        assert np.array_equal(got, want), (name, pb, s)
 
 
 @pytest.mark.parametrize("name", list(GRAPHS))
