@@ -34,6 +34,7 @@ struct BatchCtl {
     unsigned long long push_lanes;    // lanes expanded top-down this level
     unsigned long long pull_lanes;    // lanes searched bottom-up this level (BFS)
     unsigned long long lane_T[2][64]; // per-lane frontier edge count, by level parity
+    int bmp;                          // this level marks touched vertices in a bitmap
 };
 
 struct grx_batch {
@@ -46,6 +47,7 @@ struct grx_batch {
     uint32_t *E[3];
     void *R[3];
     int32_t *touched;
+    uint32_t *tbits;                  // touched bitmap of large levels
     BatchCtl *ctl;
     unsigned long long busy;          // host view of occupied lanes
     void *out_host[64];
@@ -58,8 +60,11 @@ namespace {
 
 constexpr int BT_BLOCK = 256;
 constexpr int BT_WARPS = BT_BLOCK / 32;
-constexpr int BT_ITEMS = 4;
+constexpr int BT_ITEMS = 8;
 constexpr int BT_WTILE = 32 * BT_ITEMS;
+constexpr int BTX_BLOCK = 128;                      // expansion kernel (shared memory per warp)
+constexpr int BTX_WARPS = BTX_BLOCK / 32;
+static_assert(BT_WTILE == 256, "warp_tile_rows8 covers 256-position tiles");
 constexpr double BT_PULL_FRACTION = 1.0 / 32.0;   // a lane pulls when its frontier edges > E/32
 
 template <typename T>
@@ -79,6 +84,8 @@ struct BatchArgs {
     uint32_t *E[3];
     OffT *R[3];
     int32_t *touched;
+    uint32_t *tbits;
+    int64_t words;
     BatchCtl *ctl;
 };
 
@@ -88,6 +95,7 @@ struct BtWarpSmem {
     int32_t u[BT_WTILE + 1];
     OffT rs[BT_WTILE + 1];
     unsigned long long cm[BT_WTILE + 1];
+    alignas(16) uint16_t rid[BT_WTILE];
 };
 
 // Level begin (one thread): a direction per lane (Sec. 6.1 applied lane by
@@ -106,6 +114,8 @@ __global__ void k_bt_begin(BatchArgs<OffT> a) {
     }
     c->pull_lanes = pull;
     c->push_lanes = c->active & ~pull;
+    // large levels: reductions plus a touched bitmap instead of claiming atomics
+    c->bmp = (uint32_t)c->qpack[L & 3] >= (uint32_t)(a.nv / 8);
     c->qpack[(L + 1) & 3] = 0ull;
     c->qpack[(L + 2) & 3] = 0ull;
     c->ucount[(L + 1) & 3] = 0u;
@@ -161,17 +171,16 @@ __device__ __forceinline__ int bt_load_tile(const BatchArgs<OffT> &a, const int3
 }
 
 template <typename OffT>
-__global__ void __launch_bounds__(BT_BLOCK) k_bt_expand(BatchArgs<OffT> a) {
-    __shared__ BtWarpSmem<OffT> wsm[BT_WARPS];
-    __shared__ int32_t tbufs[BT_WARPS][BT_WTILE];
+__global__ void __launch_bounds__(BTX_BLOCK) k_bt_expand(BatchArgs<OffT> a) {
+    __shared__ BtWarpSmem<OffT> wsm[BTX_WARPS];
     BatchCtl *c = a.ctl;
     const int L = c->L;
     bt_clear_prev(a, L, c->qprev);
     if (c->push_lanes == 0ull) return;
     BtWarpSmem<OffT> &w = wsm[threadIdx.x >> 5];
-    int32_t *tbuf = tbufs[threadIdx.x >> 5];
     const unsigned int lane = threadIdx.x & 31;
     const unsigned long long lanes = c->push_lanes;
+    const bool bmp = c->bmp != 0;
     const int32_t *Qv = pk3(a.Q[0], a.Q[1], a.Q[2], L % 3);
     const uint32_t *Qe = pk3(a.E[0], a.E[1], a.E[2], L % 3);
     const OffT *Qr = pk3(a.R[0], a.R[1], a.R[2], L % 3);
@@ -183,8 +192,8 @@ __global__ void __launch_bounds__(BT_BLOCK) k_bt_expand(BatchArgs<OffT> a) {
     const bool sssp = a.kind == GRX_KIND_SSSP;
     const int wtile = BT_WTILE;
     const uint64_t ntiles = (T + wtile - 1) / wtile;
-    const uint64_t nwarps = (uint64_t)gridDim.x * BT_WARPS;
-    const uint64_t gw = (uint64_t)blockIdx.x * BT_WARPS + (threadIdx.x >> 5);
+    const uint64_t nwarps = (uint64_t)gridDim.x * BTX_WARPS;
+    const uint64_t gw = (uint64_t)blockIdx.x * BTX_WARPS + (threadIdx.x >> 5);
     const uint64_t per = (ntiles + nwarps - 1) / nwarps;
     const uint64_t tb0 = gw * per, tb1 = min(ntiles, tb0 + per);
     if (tb0 >= tb1) return;
@@ -206,76 +215,69 @@ __global__ void __launch_bounds__(BT_BLOCK) k_bt_expand(BatchArgs<OffT> a) {
         const uint32_t e1 = (uint32_t)min(T, e0 + wtile);
         const int n = bt_load_tile(a, Qv, Qe, Qr, cin, lanes, q, i0, e1, wtile, w);
         const uint32_t next_start = w.qe[n];
+        int row[BT_ITEMS];
+        warp_tile_rows8(w.rid, w.qe, (uint32_t)e0, n, row);
         // each lane a run of BT_ITEMS edges; per edge the lanes to OR into
         // next[v]: BFS m & ~seen[v]; SSSP the lanes of m whose relaxation
-        // improved D[v][lane] (cost per edge = popcount of m)
-        const uint64_t t0 = e0 + (uint64_t)lane * BT_ITEMS;
+        // improves D[v][lane] (cost per edge = popcount of m)
+        const uint32_t t0 = (uint32_t)e0 + lane * BT_ITEMS;
         int32_t v[BT_ITEMS], uu[BT_ITEMS];
         uint32_t ww[BT_ITEMS];
         unsigned long long m[BT_ITEMS];
 #pragma unroll
         for (int k = 0; k < BT_ITEMS; ++k) {
-            v[k] = 0;
-            uu[k] = 0;
-            ww[k] = 0;
-            m[k] = 0ull;
+            const uint32_t e = t0 + k;
+            const int j = row[k];
+            const bool ok = e < e1;
+            const OffT idx = ok ? w.rs[j] + (OffT)(e - w.qe[j]) : (OffT)0;
+            v[k] = ok ? __ldg(a.col + idx) : 0;
+            m[k] = ok ? w.cm[j] : 0ull;
+            ww[k] = (ok && sssp) ? __ldg(a.w + idx) : 0u;
+            uu[k] = (ok && sssp) ? w.u[j] : 0;
         }
-        if (t0 < e1) {
-            int j = upper_index_smem(w.qe, n, (uint32_t)t0);
-#pragma unroll
-            for (int k = 0; k < BT_ITEMS; ++k) {
-                const uint32_t e = (uint32_t)t0 + k;
-                if (e < e1) {
-                    while (w.qe[j + 1] <= e) ++j;
-                    const OffT idx = w.rs[j] + (OffT)(e - w.qe[j]);
-                    v[k] = a.col[idx];
-                    m[k] = w.cm[j];
-                    if (sssp) {
-                        ww[k] = a.w[idx];
-                        uu[k] = w.u[j];
-                    }
-                }
-            }
-        }
-        uint32_t tm = 0;
+        __syncwarp();
+        unsigned long long mk[BT_ITEMS];
 #pragma unroll
         for (int k = 0; k < BT_ITEMS; ++k) {
-            unsigned long long mk = 0ull;
+            mk[k] = 0ull;
             if (m[k] && !sssp) {
-                mk = m[k] & ~a.seen[v[k]];
+                mk[k] = m[k] & ~__ldg(a.seen + v[k]);
             } else if (m[k]) {
                 unsigned long long bits = m[k];
                 while (bits) {
                     const int bl = __ffsll((long long)bits) - 1;
                     bits &= bits - 1;
-                    const uint64_t nd = (uint64_t)a.D[(int64_t)uu[k] * 64 + bl] + ww[k];
+                    const uint64_t nd = (uint64_t)__ldcg(a.D + (int64_t)uu[k] * 64 + bl) + ww[k];
                     if (nd >= 0xffffffffull) {
                         atomicCAS(&c->status, 0, GRX_ERANGE);
-                    } else if ((uint32_t)nd < a.D[(int64_t)v[k] * 64 + bl] &&
-                               (uint32_t)nd < atomicMin(a.D + (int64_t)v[k] * 64 + bl, (uint32_t)nd)) {
-                        mk |= 1ull << bl;
+                    } else if ((uint32_t)nd < __ldcg(a.D + (int64_t)v[k] * 64 + bl)) {
+                        if (bmp) {
+                            // a reduction: the lane did improve in this level,
+                            // by this proposal or a smaller one
+                            atomicMin(a.D + (int64_t)v[k] * 64 + bl, (uint32_t)nd);
+                            mk[k] |= 1ull << bl;
+                        } else if ((uint32_t)nd < atomicMin(a.D + (int64_t)v[k] * 64 + bl, (uint32_t)nd)) {
+                            mk[k] |= 1ull << bl;
+                        }
                     }
                 }
             }
-            if (mk && atomicOr(a.next + v[k], mk) == 0ull) tm |= 1u << k;
         }
-        const uint32_t cnt = __popc(tm);
-        uint32_t incl = cnt;
+        if (bmp) {
 #pragma unroll
-        for (int o = 1; o < 32; o <<= 1) {
-            const uint32_t y = __shfl_up_sync(GRX_FULL_MASK, incl, o);
-            if (lane >= (unsigned)o) incl += y;
+            for (int k = 0; k < BT_ITEMS; ++k) {
+                if (mk[k]) {
+                    atomicOr(a.next + v[k], mk[k]);                   // results unused: reductions
+                    atomicOr(a.tbits + (v[k] >> 5), 1u << (v[k] & 31));
+                }
+            }
+        } else {
+            uint32_t tm = 0;
+#pragma unroll
+            for (int k = 0; k < BT_ITEMS; ++k)
+                if (mk[k] && atomicOr(a.next + v[k], mk[k]) == 0ull) tm |= 1u << k;
+            warp_append_list_items<BT_ITEMS>(v, tm, a.touched, tctr);
         }
-        uint32_t p = incl - cnt;
-#pragma unroll
-        for (int k = 0; k < BT_ITEMS; ++k)
-            if (tm >> k & 1u) tbuf[p++] = v[k];
-        const int nt = (int)__shfl_sync(GRX_FULL_MASK, incl, 31);
-        __syncwarp();
-        unsigned int base = 0;
-        if (lane == 0 && nt) base = atomicAdd(tctr, (unsigned)nt);
-        base = __shfl_sync(GRX_FULL_MASK, base, 0);
-        for (int t = (int)lane; t < nt; t += 32) a.touched[base + t] = tbuf[t];
         i0 = (next_start == e1) ? i0 + n : i0 + n - 1;
         __syncwarp();
     }
@@ -311,12 +313,54 @@ __device__ __forceinline__ void lane_t_flush(LaneT &s, BatchCtl *c, int L) {
     if (threadIdx.x < 64 && s.t[threadIdx.x]) atomicAdd(&c->lane_T[(L + 1) & 1][threadIdx.x], s.t[threadIdx.x]);
 }
 
+// One touched vertex (or -1): its next mask becomes its new push lanes (BFS:
+// not yet seen; labelled here), it joins the next frontier (once), and its
+// lanes stay alive.  All 32 lanes of the warp call.
+template <typename OffT>
+__device__ __forceinline__ void bt_finish_vertex(const BatchArgs<OffT> &a, BatchCtl *c, int L,
+                                                 unsigned long long lanes, bool bfsk, int32_t vv,
+                                                 unsigned long long *cout, int32_t *Qv_out,
+                                                 uint32_t *Qe_out, OffT *Qr_out, LaneT &sT,
+                                                 unsigned long long &alive) {
+    int32_t v[1] = {vv < 0 ? 0 : vv};
+    uint32_t deg[1] = {0};
+    OffT rb[1] = {0};
+    uint32_t app = 0;
+    if (vv >= 0) {
+        const unsigned long long nx = a.next[vv];
+        a.next[vv] = 0ull;
+        unsigned long long nw = nx & lanes;
+        if (bfsk) {
+            const unsigned long long sv = a.seen[vv];
+            nw &= ~sv;
+            if (nw) {
+                a.seen[vv] = sv | nw;
+                bt_label(c, vv, nw, L);
+            }
+        }
+        if (nw) {
+            const unsigned long long before = cout[vv];
+            cout[vv] = before | nw;
+            rb[0] = a.ro[vv];
+            deg[0] = (uint32_t)(a.ro[vv + 1] - rb[0]);
+            if (deg[0]) {
+                alive |= nw;
+                lane_t_add(sT, nw, deg[0]);
+                if (before == 0ull) app = 1;
+            }
+        }
+    }
+    warp_append_items<1, OffT>(v, deg, rb, app, Qv_out, Qe_out, Qr_out, &c->qpack[(L + 1) & 3]);
+}
+
 // Touched vertices -> their new push lanes, the next frontier, the alive mask.
 // Runs after the pull kernel: a vertex the pull already put in the frontier
-// only gains lanes (no second append).
+// only gains lanes (no second append).  Large levels read the touched bitmap
+// (warps own 32-word chunks and clear them), small ones the touched list.
 template <typename OffT>
 __global__ void __launch_bounds__(BT_BLOCK) k_bt_finalize(BatchArgs<OffT> a) {
     __shared__ LaneT sT;
+    __shared__ uint16_t lists[BT_WARPS][32 * 32];
     BatchCtl *c = a.ctl;
     const int L = c->L;
     if (threadIdx.x < 64) sT.t[threadIdx.x] = 0ull;
@@ -327,41 +371,31 @@ __global__ void __launch_bounds__(BT_BLOCK) k_bt_finalize(BatchArgs<OffT> a) {
     int32_t *Qv_out = pk3(a.Q[0], a.Q[1], a.Q[2], (L + 1) % 3);
     uint32_t *Qe_out = pk3(a.E[0], a.E[1], a.E[2], (L + 1) % 3);
     OffT *Qr_out = pk3(a.R[0], a.R[1], a.R[2], (L + 1) % 3);
-    const int64_t count = c->ucount[(L + 1) & 3];
-    const int64_t span = (count + 31) & ~(int64_t)31;
     unsigned long long alive = 0ull;
-    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < span;
-         i += (int64_t)gridDim.x * blockDim.x) {
-        int32_t v[1] = {0};
-        uint32_t deg[1] = {0};
-        OffT rb[1] = {0};
-        uint32_t app = 0;
-        if (i < count) {
-            v[0] = a.touched[i];
-            const unsigned long long nx = a.next[v[0]];
-            a.next[v[0]] = 0ull;
-            unsigned long long nw = nx & lanes;
-            if (bfsk) {
-                const unsigned long long sv = a.seen[v[0]];
-                nw &= ~sv;
-                if (nw) {
-                    a.seen[v[0]] = sv | nw;
-                    bt_label(c, v[0], nw, L);
-                }
+    if (c->bmp) {
+        uint16_t *list = lists[threadIdx.x >> 5];
+        const unsigned int lane = threadIdx.x & 31;
+        const int64_t nsc = (a.words + 31) / 32;
+        const int64_t nwarps = (int64_t)gridDim.x * BT_WARPS;
+        for (int64_t sc = (int64_t)blockIdx.x * BT_WARPS + (threadIdx.x >> 5); sc < nsc; sc += nwarps) {
+            const int64_t wd = sc * 32 + lane;
+            const uint32_t bits = wd < a.words ? a.tbits[wd] : 0u;
+            if (bits) a.tbits[wd] = 0u;
+            const int n = warp_compact_bits(bits, list);
+            for (int base = 0; base < n; base += 32) {
+                const int i = base + (int)lane;
+                bt_finish_vertex<OffT>(a, c, L, lanes, bfsk, i < n ? (int32_t)(sc * 1024 + list[i]) : -1, cout,
+                                       Qv_out, Qe_out, Qr_out, sT, alive);
             }
-            if (nw) {
-                const unsigned long long before = cout[v[0]];
-                cout[v[0]] = before | nw;
-                rb[0] = a.ro[v[0]];
-                deg[0] = (uint32_t)(a.ro[v[0] + 1] - rb[0]);
-                if (deg[0]) {
-                    alive |= nw;
-                    lane_t_add(sT, nw, deg[0]);
-                    if (before == 0ull) app = 1;
-                }
-            }
+            __syncwarp();
         }
-        warp_append_items<1, OffT>(v, deg, rb, app, Qv_out, Qe_out, Qr_out, &c->qpack[(L + 1) & 3]);
+    } else {
+        const int64_t count = c->ucount[(L + 1) & 3];
+        const int64_t span = (count + 31) & ~(int64_t)31;
+        for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < span;
+             i += (int64_t)gridDim.x * blockDim.x)
+            bt_finish_vertex<OffT>(a, c, L, lanes, bfsk, i < count ? a.touched[i] : -1, cout, Qv_out, Qe_out,
+                                   Qr_out, sT, alive);
     }
     for (int o = 16; o > 0; o >>= 1) alive |= __shfl_xor_sync(GRX_FULL_MASK, alive, o);
     if ((threadIdx.x & 31) == 0 && alive) atomicOr(&c->alive, alive);
@@ -489,6 +523,7 @@ size_t batch_bytes(const grx_graph *g, int kind) {
     else b += nv * 64 * 4;                                     // D[v][64]
     b += 3 * nv * (4 + 4 + (g->off64 ? 8 : 4));                // frontier ring
     b += nv * 4 + sizeof(BatchCtl);                            // touched list, control
+    b += ((nv + 31) / 32) * 4 + 16;                             // touched bitmap
     return b;
 }
 
@@ -524,6 +559,8 @@ BatchArgs<OffT> batch_args(grx_batch *b) {
     }
     a.D = b->D;
     a.touched = b->touched;
+    a.tbits = b->tbits;
+    a.words = b->g->words;
     a.ctl = b->ctl;
     return a;
 }
@@ -533,7 +570,7 @@ grx_status batch_step_typed(grx_batch *b, int steps) {
     BatchArgs<OffT> a = batch_args<OffT>(b);
     for (int i = 0; i < steps; ++i) {
         k_bt_begin<OffT><<<1, 1, 0, b->s>>>(a);
-        k_bt_expand<OffT><<<b->blocks, BT_BLOCK, 0, b->s>>>(a);
+        k_bt_expand<OffT><<<b->blocks * (BT_BLOCK / BTX_BLOCK), BTX_BLOCK, 0, b->s>>>(a);
         if (b->kind == GRX_KIND_BFS) k_bt_pull<OffT><<<b->blocks, BT_BLOCK, 0, b->s>>>(a);
         k_bt_finalize<OffT><<<b->blocks, BT_BLOCK, 0, b->s>>>(a);
         k_bt_end<<<1, 1, 0, b->s>>>(b->ctl);
@@ -577,8 +614,9 @@ extern "C" grx_status grx_batch_open(grx_graph *g, int kind, void *stream, grx_b
     if (kind == GRX_KIND_BFS) b->seen = (unsigned long long *)batch_alloc(b, nv * 8);
     else b->D = (uint32_t *)batch_alloc(b, nv * 64 * 4);
     b->touched = (int32_t *)batch_alloc(b, nv * 4);
+    b->tbits = (uint32_t *)batch_alloc(b, ((nv + 31) / 32) * 4 + 16);
     b->ctl = (BatchCtl *)batch_alloc(b, sizeof(BatchCtl));
-    ok = ok && b->next && b->touched && b->ctl && (kind == GRX_KIND_BFS ? b->seen != nullptr : b->D != nullptr);
+    ok = ok && b->next && b->touched && b->tbits && b->ctl && (kind == GRX_KIND_BFS ? b->seen != nullptr : b->D != nullptr);
     if (!ok) {
         batch_release(b);
         return grx_fail(GRX_ENOMEM, "grx_batch_open: device allocation of %zu bytes failed",
@@ -589,6 +627,7 @@ extern "C" grx_status grx_batch_open(grx_graph *g, int kind, void *stream, grx_b
     if (e == cudaSuccess) e = cudaMemsetAsync(b->next, 0, nv * 8, b->s);
     if (e == cudaSuccess && b->seen) e = cudaMemsetAsync(b->seen, 0, nv * 8, b->s);
     if (e == cudaSuccess) e = cudaMemsetAsync(b->ctl, 0, sizeof(BatchCtl), b->s);
+    if (e == cudaSuccess) e = cudaMemsetAsync(b->tbits, 0, ((nv + 31) / 32) * 4 + 16, b->s);
     if (e != cudaSuccess) {
         batch_release(b);
         return grx_cuda_fail(e, "grx_batch_open: initialisation");

@@ -7,9 +7,13 @@
 //    use atomicMin on their own word.  The output is transposed to the
 //    caller's lane-major layout at the end.
 //  * A vertex's "changed" mask lists the lanes whose distance improved in the
-//    last round; only those lanes relax its edges.  Improved lanes are OR-ed
-//    into next[v] (one atomic per warp and edge); the first toucher lists v,
-//    and a finalize phase moves next into the frontier's masks.
+//    last round; only those lanes relax its edges.  A warp stages a tile's 64
+//    edges in shared memory (coalesced) and relaxes 8 of them at a time, all
+//    their distance loads in flight.  Improved lanes are OR-ed into next[v]
+//    (one atomic per warp and edge); the first toucher lists v -- or, in
+//    rounds with at least push_bitmap * V edges, the min and the OR are
+//    reductions and v is marked in a touched bitmap -- and a finalize phase
+//    moves next into the frontier's masks.
 //  * Frontier slots carry the degree prefix and row start (equal warp tiles of
 //    edges, as in BFS); the changed masks rotate through three arrays like the
 //    multi-source BFS lane masks.  One cooperative persistent kernel, rounds
@@ -21,7 +25,7 @@ namespace {
 constexpr int MP_BLOCK = 256;
 constexpr int MP_WARPS = MP_BLOCK / 32;
 constexpr int MP_WTILE = 64;                 // edges per warp tile
-constexpr int MP_UNROLL = 4;                 // edges relaxed together by a warp
+constexpr int MP_UNROLL = 8;                 // edges relaxed together by a warp
 
 template <typename OffT>
 struct MpArgs {
@@ -39,6 +43,9 @@ struct MpArgs {
     uint32_t *E[3];
     OffT *R[3];
     int32_t *touched;
+    uint32_t *tbits;                         // touched bitmap of large rounds
+    int64_t words;
+    uint32_t bmp_min_T;
     TravCtl *ctl;
     unsigned int *bar_flags;
     DevStats *stats;
@@ -51,6 +58,9 @@ struct MpWarpSmem {
     int32_t u[MP_WTILE + 1];
     OffT rs[MP_WTILE + 1];
     unsigned long long cm[MP_WTILE + 1];
+    int32_t ev[MP_WTILE];                    // the tile's edges: target, weight, row
+    uint32_t ew[MP_WTILE];
+    int32_t er[MP_WTILE];
 };
 
 template <typename T>
@@ -68,6 +78,7 @@ __device__ void mp_init_fill(const MpArgs<OffT> &a) {
         a.cur[1][v] = 0ull;
         a.cur[2][v] = 0ull;
     }
+    for (int64_t w = tid; w < a.words; w += stride) a.tbits[w] = 0u;
 }
 
 template <typename OffT>
@@ -100,7 +111,7 @@ namespace {
 
 template <typename OffT>
 __device__ void mp_expand(const MpArgs<OffT> &a, int L, uint32_t q, uint64_t T, MpWarpSmem<OffT> &w,
-                          int32_t *tbuf) {
+                          int32_t *tbuf, bool bmp) {
     const unsigned int lane = threadIdx.x & 31;
     const int32_t *Qv = pk3(a.Q[0], a.Q[1], a.Q[2], L % 3);
     const uint32_t *Qe = pk3(a.E[0], a.E[1], a.E[2], L % 3);
@@ -143,27 +154,33 @@ __device__ void mp_expand(const MpArgs<OffT> &a, int L, uint32_t q, uint64_t T, 
         }
         __syncwarp();
         const uint32_t next_start = w.qe[n];
-        int nt = 0;                                   // touched vertices of this tile
-        int j = 0;
-        for (uint32_t eb = (uint32_t)e0; eb < e1; eb += MP_UNROLL) {
+        // the tile's edges, two per lane, coalesced: target, weight, row
+#pragma unroll
+        for (int h = 0; h < MP_WTILE / 32; ++h) {
+            const uint32_t e = (uint32_t)e0 + lane + 32 * h;
+            if (e < e1) {
+                const int j = upper_index_smem(w.qe, n, e);
+                const OffT idx = w.rs[j] + (OffT)(e - w.qe[j]);
+                w.ev[lane + 32 * h] = __ldg(a.col + idx);
+                w.ew[lane + 32 * h] = __ldg(a.w + idx);
+                w.er[lane + 32 * h] = j;
+            }
+        }
+        __syncwarp();
+        const int len = (int)(e1 - (uint32_t)e0);
+        int nt = 0;                                   // touched vertices of this tile (list rounds)
+        for (int eb = 0; eb < len; eb += MP_UNROLL) {
             int32_t vv[MP_UNROLL], uu[MP_UNROLL];
             uint32_t ww[MP_UNROLL];
             unsigned long long mm[MP_UNROLL];
 #pragma unroll
             for (int k = 0; k < MP_UNROLL; ++k) {
-                const uint32_t e = eb + k;
-                vv[k] = 0;
-                uu[k] = 0;
-                ww[k] = 0;
-                mm[k] = 0ull;
-                if (e < e1) {
-                    while (w.qe[j + 1] <= e) ++j;
-                    const OffT idx = w.rs[j] + (OffT)(e - w.qe[j]);
-                    vv[k] = __ldg(a.col + idx);
-                    ww[k] = __ldg(a.w + idx);
-                    uu[k] = w.u[j];
-                    mm[k] = w.cm[j];
-                }
+                const bool ok = eb + k < len;
+                const int j = ok ? w.er[eb + k] : 0;
+                vv[k] = ok ? w.ev[eb + k] : 0;
+                ww[k] = ok ? w.ew[eb + k] : 0u;
+                uu[k] = ok ? w.u[j] : 0;
+                mm[k] = ok ? w.cm[j] : 0ull;
             }
             unsigned long long imp[MP_UNROLL];
 #pragma unroll
@@ -185,20 +202,37 @@ __device__ void mp_expand(const MpArgs<OffT> &a, int L, uint32_t q, uint64_t T, 
                         if (nd >= 0xffffffffull) {
                             grx_set_status(a.ctl, GRX_ERANGE);
                         } else if ((uint32_t)nd < dv[k]) {
-                            const uint32_t old = atomicMin(a.D + (int64_t)vv[k] * 64 + b, (uint32_t)nd);
-                            improved = (uint32_t)nd < old;
+                            if (bmp) {
+                                // a reduction: the lane improves in this round,
+                                // by this proposal or a smaller one
+                                atomicMin(a.D + (int64_t)vv[k] * 64 + b, (uint32_t)nd);
+                                improved = true;
+                            } else {
+                                const uint32_t old = atomicMin(a.D + (int64_t)vv[k] * 64 + b, (uint32_t)nd);
+                                improved = (uint32_t)nd < old;
+                            }
                         }
                     }
                     imp[k] |= (unsigned long long)__ballot_sync(GRX_FULL_MASK, improved) << (32 * h);
                 }
             }
+            if (bmp) {
 #pragma unroll
-            for (int k = 0; k < MP_UNROLL; ++k) {
-                bool first = false;
-                if (lane == (unsigned)k && imp[k]) first = atomicOr(a.next + vv[k], imp[k]) == 0ull;
-                const unsigned int fm = __ballot_sync(GRX_FULL_MASK, first);
-                if (first) tbuf[nt + __popc(fm & lanemask_lt())] = vv[k];
-                nt += __popc(fm);
+                for (int k = 0; k < MP_UNROLL; ++k) {
+                    if (lane == (unsigned)k && imp[k]) {
+                        atomicOr(a.next + vv[k], imp[k]);                // results unused: reductions
+                        atomicOr(a.tbits + (vv[k] >> 5), 1u << (vv[k] & 31));
+                    }
+                }
+            } else {
+#pragma unroll
+                for (int k = 0; k < MP_UNROLL; ++k) {
+                    bool first = false;
+                    if (lane == (unsigned)k && imp[k]) first = atomicOr(a.next + vv[k], imp[k]) == 0ull;
+                    const unsigned int fm = __ballot_sync(GRX_FULL_MASK, first);
+                    if (first) tbuf[nt + __popc(fm & lanemask_lt())] = vv[k];
+                    nt += __popc(fm);
+                }
             }
         }
         __syncwarp();
@@ -212,32 +246,59 @@ __device__ void mp_expand(const MpArgs<OffT> &a, int L, uint32_t q, uint64_t T, 
     }
 }
 
+// A touched vertex (or -1): its improved lanes become its changed mask in
+// the next frontier.  All 32 lanes of the warp call.
 template <typename OffT>
-__device__ void mp_finalize(const MpArgs<OffT> &a, int L) {
+__device__ __forceinline__ void mp_touched(const MpArgs<OffT> &a, int32_t vv, unsigned long long *cout,
+                                           int32_t *Qv_out, uint32_t *Qe_out, OffT *Qr_out,
+                                           unsigned long long *ctr) {
+    int32_t v[1] = {vv < 0 ? 0 : vv};
+    uint32_t deg[1] = {0};
+    OffT rb[1] = {0};
+    uint32_t app = 0;
+    if (vv >= 0) {
+        const unsigned long long nx = __ldcg(a.next + vv);
+        a.next[vv] = 0ull;
+        cout[vv] = nx & a.lanes;
+        rb[0] = __ldg(a.ro + vv);
+        deg[0] = (uint32_t)(__ldg(a.ro + vv + 1) - rb[0]);
+        if (deg[0]) app = 1;
+    }
+    warp_append_items<1, OffT>(v, deg, rb, app, Qv_out, Qe_out, Qr_out, ctr);
+}
+
+// Round phase 2: touched vertices (list, or the bitmap by warps owning 32-word
+// chunks, which clear it) become the next frontier.
+template <typename OffT>
+__device__ void mp_finalize(const MpArgs<OffT> &a, int L, bool bmp, uint16_t *list) {
     unsigned long long *cout = pk3(a.cur[0], a.cur[1], a.cur[2], (L + 1) % 3);
     int32_t *Qv_out = pk3(a.Q[0], a.Q[1], a.Q[2], (L + 1) % 3);
     uint32_t *Qe_out = pk3(a.E[0], a.E[1], a.E[2], (L + 1) % 3);
     OffT *Qr_out = pk3(a.R[0], a.R[1], a.R[2], (L + 1) % 3);
     unsigned long long *ctr = &a.ctl->qpack[(L + 1) & 3];
+    if (bmp) {
+        const unsigned int lane = threadIdx.x & 31;
+        const int64_t nsc = (a.words + 31) / 32;
+        const int64_t nwarps = (int64_t)gridDim.x * MP_WARPS;
+        for (int64_t sc = (int64_t)blockIdx.x * MP_WARPS + (threadIdx.x >> 5); sc < nsc; sc += nwarps) {
+            const int64_t wd = sc * 32 + lane;
+            const uint32_t bits = wd < a.words ? __ldcg(a.tbits + wd) : 0u;
+            if (bits) a.tbits[wd] = 0u;
+            const int n = warp_compact_bits(bits, list);
+            for (int base = 0; base < n; base += 32) {
+                const int i = base + (int)lane;
+                mp_touched<OffT>(a, i < n ? (int32_t)(sc * 1024 + list[i]) : -1, cout, Qv_out, Qe_out, Qr_out,
+                                 ctr);
+            }
+            __syncwarp();
+        }
+        return;
+    }
     const int64_t count = ld_relaxed_u32(&a.ctl->ucount[(L + 1) & 3]);
     const int64_t span = (count + 31) & ~(int64_t)31;
     for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < span;
-         i += (int64_t)gridDim.x * blockDim.x) {
-        int32_t v[1] = {0};
-        uint32_t deg[1] = {0};
-        OffT rb[1] = {0};
-        uint32_t app = 0;
-        if (i < count) {
-            v[0] = __ldcg(a.touched + i);
-            const unsigned long long nx = __ldcg(a.next + v[0]);
-            a.next[v[0]] = 0ull;
-            cout[v[0]] = nx & a.lanes;
-            rb[0] = __ldg(a.ro + v[0]);
-            deg[0] = (uint32_t)(__ldg(a.ro + v[0] + 1) - rb[0]);
-            if (deg[0]) app = 1;
-        }
-        warp_append_items<1, OffT>(v, deg, rb, app, Qv_out, Qe_out, Qr_out, ctr);
-    }
+         i += (int64_t)gridDim.x * blockDim.x)
+        mp_touched<OffT>(a, i < count ? __ldcg(a.touched + i) : -1, cout, Qv_out, Qe_out, Qr_out, ctr);
 }
 
 }  // namespace
@@ -248,6 +309,7 @@ template <typename OffT>
 __global__ void __launch_bounds__(MP_BLOCK, 2) k_mssp_persistent(MpArgs<OffT> a) {
     __shared__ MpWarpSmem<OffT> wsm[MP_WARPS];
     __shared__ int32_t tbufs[MP_WARPS][MP_WTILE];
+    __shared__ uint16_t lists[MP_WARPS][32 * 32];
     __shared__ uint32_t s_q, s_T;
     __shared__ int s_done;
     const int wi = threadIdx.x >> 5;
@@ -281,9 +343,10 @@ __global__ void __launch_bounds__(MP_BLOCK, 2) k_mssp_persistent(MpArgs<OffT> a)
                  i += (int64_t)gridDim.x * blockDim.x)
                 cp[__ldcg(Qp + i)] = 0ull;
         }
-        mp_expand(a, L, q, T, wsm[wi], tbufs[wi]);
+        const bool bmp = T >= a.bmp_min_T;
+        mp_expand(a, L, q, T, wsm[wi], tbufs[wi], bmp);
         if (!flag_barrier(bar)) return;
-        mp_finalize(a, L);
+        mp_finalize(a, L, bmp, lists[wi]);
         if (!flag_barrier(bar)) return;
         qprev = q;
     }
@@ -326,6 +389,13 @@ grx_status mp_launch_typed(grx_graph *g, const int32_t *srcs, int n, uint32_t *d
         a.R[i] = (OffT *)g->qr[i];
     }
     a.touched = g->ulist[0];
+    a.tbits = g->ms_tbits;
+    a.words = g->words;
+    {   // reduction rounds when a round's edges reach push_bitmap * nv (0 = 1/8, < 0 = never)
+        const double pb = o->push_bitmap == 0.f ? 0.125 : (double)o->push_bitmap;
+        const double t = pb * (double)g->nv;
+        a.bmp_min_T = pb < 0 ? 0xffffffffu : (t < 1.0 ? 1u : (t > 4294967295.0 ? 0xffffffffu : (uint32_t)t));
+    }
     a.ctl = g->ctl;
     a.bar_flags = g->bar_flags;
     a.stats = g->stats;
@@ -358,6 +428,11 @@ grx_status grx_mssp_launch(grx_graph *g, const int32_t *srcs, int n, uint32_t *d
     if (!g->ms_dist) {
         g->ms_dist = (uint32_t *)grx_alloc(g, (size_t)g->nv * 64 * sizeof(uint32_t), s);
         if (!g->ms_dist) return grx_fail(GRX_ENOMEM, "sssp_multi: distance workspace allocation failed");
+    }
+    if (!g->ms_tbits) {
+        g->ms_tbits = (uint32_t *)grx_alloc(g, (size_t)g->words * 4 + 16, s);
+        if (!g->ms_tbits) return grx_fail(GRX_ENOMEM, "sssp_multi: touched bitmap allocation failed");
+        GRX_CUDA(cudaMemsetAsync(g->ms_tbits, 0, (size_t)g->words * 4 + 16, s));
     }
     return g->off64 ? mp_launch_typed<int64_t>(g, srcs, n, dist, o, s)
                     : mp_launch_typed<int32_t>(g, srcs, n, dist, o, s);

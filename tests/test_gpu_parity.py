@@ -341,15 +341,16 @@ def test_bfs_multi_few_lanes_and_stats(grx, loaded):
 
 
 @pytest.mark.parametrize("name", ["rmat10", "rmat13", "rmat14_ef4", "grid64", "path", "star", "disconnected"])
-def test_sssp_multi_lanes_match_oracle(grx, loaded, name):
+@pytest.mark.parametrize("pb", list(PUSH_BITMAP))
+def test_sssp_multi_lanes_match_oracle(grx, loaded, name, pb):
     g, dg = GRAPHS[name], loaded[name]
     srcs = _sources(g, 40, seed=3) if name != "disconnected" else [1, 5, 10, 30, 0]
     srcs = srcs + [srcs[0], g.nv - 1]
-    d = grx.sssp_multi(dg, srcs).cpu().numpy().view(np.uint32)
+    d = grx.sssp_multi(dg, srcs, opts=grx.opts(push_bitmap=PUSH_BITMAP[pb])).cpu().numpy().view(np.uint32)
     grx.graph_status(dg)
     for b, s in enumerate(srcs):
         want = oracle.sssp(g.row_offsets, g.col_indices, g.weights, s)
-        assert np.array_equal(d[b], want), (name, b, s)
+        assert np.array_equal(d[b], want), (name, pb, b, s)
 
 
 def test_multi_source_on_the_6_vertex_union(grx):
