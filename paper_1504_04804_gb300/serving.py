@@ -1,4 +1,4 @@
-"""Continuous-batching query server over resident graphs.
+"""Continuous-batching query servers over resident graphs.
 
 Graphs stay loaded on the GPU.  Requests (a BFS or SSSP query: graph, source)
 arrive over time.  Each (graph, kind) pair has one or more 64-lane batches
@@ -19,6 +19,10 @@ run concurrently on the device.  The loop:
 Each query's result is exactly its single-source result (tests check alone
 vs. in the mix).  ``run_one_at_a_time`` is the baseline: the same requests
 served FIFO by single-source calls on one stream of the same GPU.
+
+``TraversalServer`` batches at traversal boundaries instead: requests that
+arrive while a traversal runs join the next multi-source traversal of their
+graph and kind (one persistent kernel for up to 64 lanes).
 """
 from __future__ import annotations
 
@@ -233,6 +237,130 @@ class Server:
         for s in self.slots:
             s.batch.close()
         self.slots = []
+
+
+def plan_job(pending: dict, sssp_multi_min: int = 24, lanes: int = 64, busy=()):
+    """Pure policy of the traversal-boundary server (host logic, testable
+    without a GPU).  pending: (graph, kind) -> requests in arrival order;
+    busy: graphs with a traversal in flight (a graph's workspace serves one
+    traversal at a time).  The key whose oldest request arrived first is
+    served next: BFS requests (up to `lanes`) share one multi-source traversal
+    when there are two or more, SSSP requests when at least `sssp_multi_min`
+    wait (a batched SSSP lane costs less than a single-source traversal only
+    in a full batch); otherwise the oldest request runs alone.  Returns
+    (key, requests, multi) or None when nothing can start."""
+    keys = [k for k, v in pending.items() if v and k[0] not in busy]
+    if not keys:
+        return None
+    key = min(keys, key=lambda k: (pending[k][0].arrival, pending[k][0].rid))
+    waiting = pending[key]
+    thresh = 2 if key[1] == "bfs" else sssp_multi_min
+    if len(waiting) >= thresh:
+        return key, waiting[:lanes], True
+    return key, waiting[:1], False
+
+
+class TraversalServer:
+    """Continuous batching at traversal boundaries: requests that arrive while
+    a traversal runs join the next one of their graph and kind, which the
+    persistent multi-source kernels run (64 lanes, one launch).  Compared with
+    joining at level boundaries (``Server``) a request may wait for the
+    traversal in flight, but every level costs one grid barrier instead of a
+    host round trip and several launches.  Graph handles are independent:
+    each has its own workspace, stream and one traversal in flight, so
+    traversals of different graphs (or of replica handles of one graph) run
+    side by side, each on a share of the persistent grid while other work
+    waits (a small graph's levels are as fast on a third of the SMs), on the
+    whole grid when it runs alone.  Each query's result is
+    its single-source result (tests check alone vs. in the mix)."""
+
+    def __init__(self, graphs: dict, degrees: dict, sssp_multi_min: int = 24,
+                 keep_results: bool = False, replicas: dict | None = None):
+        """replicas: graph name -> extra loaded handles of the same graph
+        (each with its own workspace), so that several traversals of one
+        graph can be in flight."""
+        import torch
+
+        from . import grx
+        self.torch, self.grx = torch, grx
+        self.degrees = degrees
+        self.sssp_multi_min = sssp_multi_min
+        self.keep = keep_results
+        self.handles = {name: [g] + list((replicas or {}).get(name, [])) for name, g in graphs.items()}
+        self.streams = {(name, i): torch.cuda.Stream() for name, hs in self.handles.items()
+                        for i in range(len(hs))}
+        props = torch.cuda.get_device_properties(torch.cuda.current_device())
+        full = props.multi_processor_count * 3
+        # grid share while other traversals run: a third of the persistent
+        # grid, half for the largest graphs (their levels scale with the SMs)
+        big = max(g.ne for g in graphs.values())
+        self.share = {name: max(1, full // 2 if g.ne * 4 >= big else full // 3) for name, g in graphs.items()}
+
+    def _launch(self, slot, key, reqs, multi, grid_blocks):
+        grx, torch = self.grx, self.torch
+        g = self.handles[key[0]][slot[1]]
+        st = self.streams[slot]
+        o = grx.opts(grid_blocks=grid_blocks)
+        with torch.cuda.stream(st):
+            srcs = [r.src for r in reqs]
+            if key[1] == "bfs":
+                out = grx.bfs_multi(g, srcs, opts=o, stream=st) if multi else \
+                    grx.bfs(g, srcs[0], opts=o, stream=st).view(1, -1)
+                reached = out >= 0
+            else:
+                out = grx.sssp_multi(g, srcs, opts=o, stream=st) if multi else \
+                    grx.sssp(g, srcs[0], opts=o, stream=st).view(1, -1)
+                reached = out != -1                  # UINT32_MAX bits read as int32 -1
+            edges = (reached.to(torch.int64) * self.degrees[key[0]].to(torch.int64)).sum(dim=1)
+            ev = torch.cuda.Event()
+            ev.record(st)
+        return out, edges, ev
+
+    def run(self, requests: list[Request], realtime: bool = True) -> dict:
+        torch = self.torch
+        order = sorted(requests, key=lambda r: r.arrival)
+        pending: dict = {}
+        nxt = 0
+        jobs: dict = {}                               # (graph, replica) -> (requests, out, edges, event)
+        t0 = time.perf_counter()
+        while nxt < len(order) or jobs or any(pending.values()):
+            now = time.perf_counter() - t0
+            while nxt < len(order) and (order[nxt].arrival <= now or not realtime):
+                r = order[nxt]
+                pending.setdefault((r.graph, r.kind), []).append(r)
+                nxt += 1
+            for slot in list(jobs):
+                reqs, out, edges, ev = jobs[slot]
+                if not ev.query():
+                    continue
+                done = time.perf_counter() - t0
+                e = edges.cpu().tolist()
+                for i, r in enumerate(reqs):
+                    r.done = done
+                    r.edges = int(e[i])
+                    if self.keep:
+                        r.result = out[i].clone()
+                del jobs[slot]
+            while True:
+                busy = {name for name, hs in self.handles.items()
+                        if all((name, i) in jobs for i in range(len(hs)))}
+                plan = plan_job(pending, self.sssp_multi_min, busy=busy)
+                if plan is None:
+                    break
+                key, reqs, multi = plan
+                pending[key] = pending[key][len(reqs):]
+                slot = next((key[0], i) for i in range(len(self.handles[key[0]])) if (key[0], i) not in jobs)
+                others = bool(jobs) or any(v for k, v in pending.items() if v and k != key)
+                for r in reqs:
+                    r.admitted = now
+                out, edges, ev = self._launch(slot, key, reqs, multi, self.share[key[0]] if others else 0)
+                jobs[slot] = (reqs, out, edges, ev)
+            if not jobs and nxt < len(order) and realtime:
+                wait = order[nxt].arrival - (time.perf_counter() - t0)
+                if wait > 2e-4:
+                    time.sleep(min(wait - 1e-4, 0.01))
+        torch.cuda.synchronize()
+        return summarize(requests, time.perf_counter() - t0)
 
 
 def summarize(requests: list[Request], wall: float) -> dict:

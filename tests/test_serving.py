@@ -138,3 +138,57 @@ def test_server_rejects_when_nothing_fits(gpu):
     srv = serving.Server(graphs, degrees, budget_bytes=1024)
     with pytest.raises(RuntimeError, match="admission impossible"):
         srv.run(reqs, realtime=False)
+
+
+def test_plan_job_oldest_key_first_and_batch_thresholds():
+    def reqs(key, times, base):
+        return [serving.Request(base + i, key[0], key[1], 0, t) for i, t in enumerate(times)]
+    pend = {("a", "bfs"): reqs(("a", "bfs"), [0.3, 0.4], 0),
+            ("b", "sssp"): reqs(("b", "sssp"), [0.1, 0.2, 0.5], 10),
+            ("c", "bfs"): []}
+    key, batch, multi = serving.plan_job(pend, sssp_multi_min=3)
+    assert key == ("b", "sssp") and multi and [r.rid for r in batch] == [10, 11, 12]
+    key, batch, multi = serving.plan_job(pend, sssp_multi_min=4)
+    assert key == ("b", "sssp") and not multi and [r.rid for r in batch] == [10]
+    pend[("b", "sssp")] = []
+    key, batch, multi = serving.plan_job(pend)
+    assert key == ("a", "bfs") and multi and len(batch) == 2
+    pend[("a", "bfs")] = reqs(("a", "bfs"), [0.3], 0)
+    assert serving.plan_job(pend)[2] is False                     # one BFS request runs alone
+    many = {("a", "bfs"): reqs(("a", "bfs"), [i * 1e-3 for i in range(100)], 0)}
+    assert len(serving.plan_job(many)[1]) == 64                   # at most 64 lanes
+    assert serving.plan_job({("a", "bfs"): []}) is None
+
+
+@pytest.mark.gpu
+def test_traversal_server_results_same_alone_and_in_the_mix(gpu):
+    torch, grx = gpu
+    hg = _graphs()
+    graphs = {k: grx.load(v) for k, v in hg.items()}
+    degrees = {k: torch.from_numpy(np.diff(v.row_offsets).astype(np.int32)).cuda() for k, v in hg.items()}
+    reqs = serving.make_requests({k: (v.row_offsets, True) for k, v in hg.items()}, 300,
+                                 rate_qps=20000.0, seed=6)
+    srv = serving.TraversalServer(graphs, degrees, sssp_multi_min=4, keep_results=True)
+    stats = srv.run(reqs)
+    assert stats["queries"] == 300 and stats["p99_ms"] >= stats["p50_ms"] > 0
+    for r in reqs:
+        g = hg[r.graph]
+        got = r.result.cpu().numpy()
+        if r.kind == "bfs":
+            want = oracle.bfs(g.row_offsets, g.col_indices, r.src)
+            assert np.array_equal(got, want), r
+            assert r.edges == int(np.diff(g.row_offsets)[want >= 0].sum())
+        else:
+            want = oracle.sssp(g.row_offsets, g.col_indices, g.weights, r.src)
+            assert np.array_equal(got.view(np.uint32), want), r
+    for r in reqs[:20]:
+        alone = grx.bfs(graphs[r.graph], r.src) if r.kind == "bfs" else grx.sssp(graphs[r.graph], r.src)
+        assert np.array_equal(alone.cpu().numpy(), r.result.cpu().numpy())
+
+
+def test_plan_job_skips_graphs_with_a_traversal_in_flight():
+    pend = {("a", "bfs"): [serving.Request(0, "a", "bfs", 0, 0.1)],
+            ("b", "bfs"): [serving.Request(1, "b", "bfs", 0, 0.2)]}
+    assert serving.plan_job(pend)[0] == ("a", "bfs")
+    assert serving.plan_job(pend, busy={"a"})[0] == ("b", "bfs")
+    assert serving.plan_job(pend, busy={"a", "b"}) is None
