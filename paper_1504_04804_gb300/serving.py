@@ -335,11 +335,14 @@ class TraversalServer:
                     continue
                 done = time.perf_counter() - t0
                 e = edges.cpu().tolist()
-                for i, r in enumerate(reqs):
-                    r.done = done
-                    r.edges = int(e[i])
-                    if self.keep:
-                        r.result = out[i].clone()
+                # copies are made on the job's stream: its output memory goes back to
+                # that stream's pool and is reused by the stream's next job
+                with torch.cuda.stream(self.streams[slot]):
+                    for i, r in enumerate(reqs):
+                        r.done = done
+                        r.edges = int(e[i])
+                        if self.keep:
+                            r.result = out[i].clone()
                 del jobs[slot]
             while True:
                 busy = {name for name, hs in self.handles.items()
