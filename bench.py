@@ -540,7 +540,7 @@ def grid_workload(args):
 
 
 def serving_bench(graphs: dict, degrees: dict, host_ro: dict, n_queries: int, seed: int = 7,
-                  loads=(0.5, 0.75, 1.0, 1.5, 2.0, 4.0), replicas: dict | None = None) -> dict:
+                  loads=(0.5, 0.6, 0.7, 0.8, 1.0, 1.5, 2.0), replicas: dict | None = None) -> dict:
     """Mixed BFS/SSSP queries with Poisson arrivals over resident graphs.
     mu = one-at-a-time saturation rate (all queries queued at once, after a
     warm-up pass); SLO = the one-at-a-time p99 at 0.5*mu; both batched

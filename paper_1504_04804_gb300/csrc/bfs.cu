@@ -72,6 +72,9 @@ constexpr int PULL_LIGHT = GRX_PULL_LIGHT;          // neighbours probed per ver
 #define GRX_PULL_PER_LANE 4
 #endif
 constexpr int PULL_PER_LANE = GRX_PULL_PER_LANE;    // candidates per lane per round
+#ifndef GRX_PULL_PREFETCH
+#define GRX_PULL_PREFETCH 1                         // next round's row offsets in flight early
+#endif
 constexpr int PULL_WCH = 32 * PULL_PER_LANE;        // candidates per warp round
 constexpr int PULL_HITEMS = PUSH_ITEMS;             // heavy-phase edges per lane per step
 constexpr int PULL_HSTEP = 32 * PULL_HITEMS;        // heavy-phase edges per warp step
@@ -514,26 +517,37 @@ __device__ void pull_level(const BfsArgs<OffT> &a, const LevelState &st, PullWar
         if (own && st.fclear) Fold[wd] = 0u;
         w.fb[lane] = 0u;
         const int n = warp_compact_bits(cand, w.list);
-        for (int base = 0; base < n; base += PULL_WCH) {
-            // 1. candidates: lane takes entries base + k*32 + lane
-            int32_t v[PULL_PER_LANE];
+        // 1. candidates: lane takes entries base + k*32 + lane; the next
+        // round's row offsets are requested before this round's probes
+        int32_t vn[PULL_PER_LANE];
+        OffT bn[PULL_PER_LANE], en[PULL_PER_LANE];
 #pragma unroll
-            for (int k = 0; k < PULL_PER_LANE; ++k) {
-                const int i = base + k * 32 + (int)lane;
-                v[k] = i < n ? (int32_t)(sc * SC_VERTS + w.list[i]) : -1;
-            }
-            // 2. light phase
+        for (int k = 0; k < PULL_PER_LANE; ++k) {
+            const int i = k * 32 + (int)lane;
+            vn[k] = i < n ? (int32_t)(sc * SC_VERTS + w.list[i]) : -1;
+            bn[k] = vn[k] >= 0 ? __ldg(a.ro + vn[k]) : (OffT)0;
+            en[k] = vn[k] >= 0 ? __ldg(a.ro + vn[k] + 1) : (OffT)0;
+        }
+        for (int base = 0; base < n; base += PULL_WCH) {
+            int32_t v[PULL_PER_LANE];
             OffT b[PULL_PER_LANE];
             uint32_t deg[PULL_PER_LANE];
 #pragma unroll
             for (int k = 0; k < PULL_PER_LANE; ++k) {
-                b[k] = 0;
-                deg[k] = 0;
-                if (v[k] >= 0) {
-                    b[k] = __ldg(a.ro + v[k]);
-                    deg[k] = (uint32_t)(__ldg(a.ro + v[k] + 1) - b[k]);
-                }
+                v[k] = vn[k];
+                b[k] = bn[k];
+                deg[k] = (uint32_t)(en[k] - bn[k]);
             }
+#if GRX_PULL_PREFETCH
+#pragma unroll
+            for (int k = 0; k < PULL_PER_LANE; ++k) {
+                const int i = base + PULL_WCH + k * 32 + (int)lane;
+                vn[k] = i < n ? (int32_t)(sc * SC_VERTS + w.list[i]) : -1;
+                bn[k] = vn[k] >= 0 ? __ldg(a.ro + vn[k]) : (OffT)0;
+                en[k] = vn[k] >= 0 ? __ldg(a.ro + vn[k] + 1) : (OffT)0;
+            }
+#endif
+            // 2. light phase
             static_assert(PULL_LIGHT == 1 || PULL_LIGHT == 2, "light phase probes 1 or 2 neighbours");
             int32_t u0[PULL_PER_LANE], u1[PULL_PER_LANE];
 #pragma unroll
@@ -633,6 +647,15 @@ __device__ void pull_level(const BfsArgs<OffT> &a, const LevelState &st, PullWar
                 }
                 __syncwarp();
             }
+#if !GRX_PULL_PREFETCH
+#pragma unroll
+            for (int k = 0; k < PULL_PER_LANE; ++k) {
+                const int i = base + PULL_WCH + k * 32 + (int)lane;
+                vn[k] = i < n ? (int32_t)(sc * SC_VERTS + w.list[i]) : -1;
+                bn[k] = vn[k] >= 0 ? __ldg(a.ro + vn[k]) : (OffT)0;
+                en[k] = vn[k] >= 0 ? __ldg(a.ro + vn[k] + 1) : (OffT)0;
+            }
+#endif
             // 4. label the found vertices; their bits go to the chunk's word masks
 #pragma unroll
             for (int k = 0; k < PULL_PER_LANE; ++k) {

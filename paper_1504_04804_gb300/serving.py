@@ -275,7 +275,8 @@ class TraversalServer:
     its single-source result (tests check alone vs. in the mix)."""
 
     def __init__(self, graphs: dict, degrees: dict, sssp_multi_min: int = 24,
-                 keep_results: bool = False, replicas: dict | None = None):
+                 keep_results: bool = False, replicas: dict | None = None,
+                 share_big: int = 2, share_small: int = 4):
         """replicas: graph name -> extra loaded handles of the same graph
         (each with its own workspace), so that several traversals of one
         graph can be in flight."""
@@ -291,10 +292,12 @@ class TraversalServer:
                         for i in range(len(hs))}
         props = torch.cuda.get_device_properties(torch.cuda.current_device())
         full = props.multi_processor_count * 3
-        # grid share while other traversals run: a third of the persistent
-        # grid, half for the largest graphs (their levels scale with the SMs)
+        # grid share while other traversals run: 1/share_small of the
+        # persistent grid, 1/share_big for the largest graphs (their levels
+        # scale with the SMs); 1 = the whole grid
         big = max(g.ne for g in graphs.values())
-        self.share = {name: max(1, full // 2 if g.ne * 4 >= big else full // 3) for name, g in graphs.items()}
+        self.share = {name: max(1, full // (share_big if g.ne * 4 >= big else share_small))
+                      for name, g in graphs.items()}
 
     def _launch(self, slot, key, reqs, multi, grid_blocks):
         grx, torch = self.grx, self.torch
