@@ -73,7 +73,7 @@ constexpr int PULL_LIGHT = GRX_PULL_LIGHT;          // neighbours probed per ver
 #endif
 constexpr int PULL_PER_LANE = GRX_PULL_PER_LANE;    // candidates per lane per round
 #ifndef GRX_PULL_PREFETCH
-#define GRX_PULL_PREFETCH 1                         // next round's row offsets in flight early
+#define GRX_PULL_PREFETCH 0                         // 1: next round's row offsets requested early (spills; slower at R-MAT 26)
 #endif
 constexpr int PULL_WCH = 32 * PULL_PER_LANE;        // candidates per warp round
 constexpr int PULL_HITEMS = PUSH_ITEMS;             // heavy-phase edges per lane per step
