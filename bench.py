@@ -81,8 +81,24 @@ def pr_bytes(nv: int, ne: int, off_bytes: int, iters: int) -> int:
     return iters * (nv * (off_bytes + 12) + ne * 8)
 
 
-def cc_bytes(nv: int, ne: int, off_bytes: int, rounds: int) -> int:
-    return rounds * (ne * 12 + nv * (off_bytes + 4)) + max(rounds - 1, 0) * nv * 8
+def msbfs_bytes(stats: dict, nv: int, off_bytes: int, lanes: int) -> int:
+    """64-lane multi-source BFS: push level |active|(2o+8) + E_exam(4+8+8);
+    pull level V_scanned(2o+8) + E_exam(4+12); plus the lane-major depth
+    output, 4 bytes per (lane, vertex)."""
+    total = 4 * lanes * nv
+    for i in range(len(stats["dir"])):
+        if stats["dir"][i] == 0:
+            total += stats["frontier"][i] * (2 * off_bytes + 8) + stats["edges_examined"][i] * 20
+        else:
+            total += stats["vertices_scanned"][i] * (2 * off_bytes + 8) + stats["edges_examined"][i] * 16
+    return total
+
+
+def cc_bytes(nv: int, hooked: int, off_bytes: int) -> int:
+    """Hooking passes (first neighbour, second neighbour, the rest outside the
+    largest component): 12 bytes per hooked edge (column, two labels) and a
+    row pass each; three compressions of 8 bytes per vertex."""
+    return hooked * 12 + 3 * nv * (off_bytes + 4) + 3 * nv * 8
 
 
 # ---------------------------------------------------------------------------
@@ -621,7 +637,12 @@ def other_primitives(grx, g, srcs, nv, ne, off_bytes, deg_h, flush, stream, peak
     lab = torch.empty(nv, dtype=torch.int32, device=flush.device)
     ts = timed(lambda i: grx.cc(g, label_out=lab), 3)
     grx.graph_status(g)
-    out["cc"] = {"ms": ts, "gteps": ne / (statistics.median(ts) / 1e3) / 1e9}
+    cst = grx.last_stats(g)
+    n_act = int(np.count_nonzero(deg_h))
+    hooked = 2 * n_act + int(cst["edges_examined"][0]) if cst["levels"] else 0
+    out["cc"] = {"ms": ts, "gteps": ne / (statistics.median(ts) / 1e3) / 1e9, "edges_hooked": hooked,
+                 "roofline_frac": cc_bytes(nv, hooked, off_bytes) / (statistics.median(ts) / 1e3) / 1e9
+                 / peak}
     # 64-lane multi-source BFS and batched SSSP (one launch each)
     from paper_1504_04804_gb300 import inputs
     lanes =[int(s) for s in inputs.pick_sources(np.concatenate([[0], np.cumsum(deg_h)]), 64, seed=11)]
@@ -629,8 +650,11 @@ def other_primitives(grx, g, srcs, nv, ne, off_bytes, deg_h, flush, stream, peak
     grx.bfs_multi(g, lanes, depth_out=dm)
     ms_edges = int(sum(int(deg_h[row >= 0].sum()) for row in dm.view(64, nv).cpu().numpy()))
     ts = timed(lambda i: grx.bfs_multi(g, lanes, depth_out=dm), 3)
+    grx.bfs_multi(g, lanes, depth_out=dm, opts=grx.opts(collect_stats=1))
+    mb = msbfs_bytes(grx.last_stats(g), nv, off_bytes, 64)
     out["bfs_multi_64"] = {"ms": ts, "gteps": ms_edges / (statistics.median(ts) / 1e3) / 1e9,
-                           "per_query_ms": statistics.median(ts) / 64}
+                           "per_query_ms": statistics.median(ts) / 64,
+                           "roofline_frac": mb / (statistics.median(ts) / 1e3) / 1e9 / peak}
     if g.weighted:
         dd = torch.empty(16 * nv, dtype=torch.int32, device=flush.device)
         ts = timed(lambda i: grx.sssp_multi(g, lanes[:16], dist_out=dd), 2)

@@ -230,7 +230,9 @@ typedef struct {
 } grx_trav_stats;
 
 /* Synchronise `stream` and copy the counters of the graph's last traversal
- * that ran with collect_stats = 1. */
+ * that ran with collect_stats = 1.  After cc (which always counts), only
+ * `levels` is set: the number of hooking rounds.  For multi-source BFS pull
+ * levels, vertices_scanned counts the rows of the edge tiles not skipped. */
 grx_status grx_last_stats(grx_graph *g, void *stream, grx_trav_stats *out);
 
 /* ---- seeded input generation (device twins of the host generators) ------ */

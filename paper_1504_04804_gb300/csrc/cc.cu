@@ -1,44 +1,41 @@
-// Connected components (Table 1; Soman et al.'s GPU CC): rounds of hooking
-// over every edge followed by pointer jumping, until a round hooks nothing.
+// Connected components (Table 1; Soman et al.'s GPU CC): hooking of trees
+// along edges with pointer jumping, labels = the minimum vertex id of each
+// component.
 //
-//  * label[v] starts at v.  Hooking: for an undirected edge (u, v) with u < v,
-//    find both roots; if they differ, atomicMin the larger root's parent to
-//    the smaller root.  Parents only ever decrease and point to a smaller id
-//    in the same component, so the forest stays acyclic and the final root of
-//    a component is its minimum vertex id -- the canonical label.
-//  * Jumping: every vertex follows parents to its root and stores it, so the
-//    next round's finds are one step.
-//  * The edge loop uses the active list (non-isolated vertices), whose edge
-//    prefix is the CSR offsets: tiles of equal edge count (first row and row
-//    count of each tile cached per graph), row of each edge by binary search
-//    in shared memory, coalesced column reads.
-//  * One persistent cooperative kernel; hook and jump phases are separated by
-//    bounded grid barriers.  Isolated vertices keep label = own id.
+//  * label[v] starts at v.  Hooking an edge (u, v) joins the trees of u and
+//    v: the larger root is hooked under the smaller one with a compare and
+//    swap that succeeds only while the larger one is still a root (else the
+//    hook retries from the new roots).  Parents only ever decrease and point
+//    to a smaller id in the same component, so the forest stays acyclic and
+//    the final root of a component is its minimum vertex id -- the canonical
+//    label.
+//  * Pointer jumping (compression) makes every vertex point at its root.
+//  * Most edges need no hooking at all (the sampling refinement of hooking
+//    of Sutton et al., Afforest, IPDPS 2018): after hooking every vertex to
+//    its first two neighbours and compressing, the largest component is found
+//    from a sample of vertices; only the vertices outside it hook the rest of
+//    their edges.  An edge between the largest component and another one is
+//    still hooked, from its endpoint outside (the graph is symmetric).
+//  * One persistent cooperative kernel; phases separated by bounded grid
+//    barriers.  Isolated vertices keep label = own id.
 #include "grx_internal.cuh"
 
 namespace {
 
 constexpr int CC_BLOCK = 256;
-constexpr int CC_ITEMS = 8;
-constexpr int CC_TILE = CC_BLOCK * CC_ITEMS;
+constexpr int CC_SAMPLES = 1024;              // vertices sampled for the largest component
 
 struct CcArgs {
     int32_t nv;
-    int64_t ne;
     const int32_t *col;
     const int32_t *active;
     const uint32_t *aoff;
-    const int2 *tiles;
+    int64_t n_active;
     int32_t *label;
     TravCtl *ctl;
+    DevStats *stats;
     unsigned int *bar_flags;
     unsigned long long timeout_ns;
-};
-
-struct CcSmem {
-    uint32_t qe[CC_TILE + 1];
-    int32_t u[CC_TILE + 1];
-    int changed;
 };
 
 __device__ __forceinline__ int32_t find_root(int32_t *label, int32_t x) {
@@ -50,71 +47,102 @@ __device__ __forceinline__ int32_t find_root(int32_t *label, int32_t x) {
     return x;
 }
 
-__device__ void hook_phase(const CcArgs &a, int round, CcSmem &sm) {
-    const uint64_t T = (uint64_t)a.ne;
-    const uint64_t ntiles = (T + CC_TILE - 1) / CC_TILE;
-    int changed = 0;
-    for (uint64_t tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
-        const uint64_t e0 = tile * CC_TILE;
-        const uint64_t e1 = min(T, e0 + CC_TILE);
-        const int2 tr = __ldg(a.tiles + tile);
-        const int64_t i0 = tr.x;
-        const int n = tr.y;
-        for (int j = threadIdx.x; j < n; j += CC_BLOCK) {
-            sm.qe[j] = __ldg(a.aoff + i0 + j);
-            sm.u[j] = __ldg(a.active + i0 + j);
+// Joins the trees of u and v: the larger root goes under the smaller one.
+// Every failed attempt means some parent decreased, so the loop ends; the cap
+// only guards against a corrupted label array (then the status is set).
+__device__ __forceinline__ void hook(int32_t *label, int32_t u, int32_t v, TravCtl *ctl) {
+    int32_t p1 = __ldcg(label + u), p2 = __ldcg(label + v);
+    for (int tries = 0; p1 != p2; ++tries) {
+        if (tries > (1 << 24)) {
+            grx_set_status(ctl, GRX_ETIMEOUT);
+            return;
         }
-        __syncthreads();
-        for (int k = 0; k < CC_ITEMS; ++k) {
-            const uint64_t e = e0 + (uint64_t)(k * CC_BLOCK + threadIdx.x);
-            if (e >= e1) break;
-            const int32_t v = __ldg(a.col + e);
-            const int32_t u = sm.u[upper_index_smem(sm.qe, n, (uint32_t)e)];
-            if (u >= v) continue;                 // each undirected edge once
-            int32_t ru = find_root(a.label, u);
-            int32_t rv = find_root(a.label, v);
-            if (ru != rv) {
-                int32_t hi = ru > rv ? ru : rv, lo = ru ^ rv ^ hi;
-                atomicMin(a.label + hi, lo);
-                changed = 1;
-            }
-        }
-        __syncthreads();
+        const int32_t hi = p1 > p2 ? p1 : p2, lo = p1 ^ p2 ^ hi;
+        const int32_t ph = __ldcg(label + hi);
+        if (ph == lo) return;                                   // already joined
+        if (ph == hi && atomicCAS(label + hi, hi, lo) == hi) return;
+        p1 = __ldcg(label + __ldcg(label + hi));                // hi moved on: retry from there
+        p2 = __ldcg(label + lo);
     }
-    changed = __syncthreads_or(changed);
-    if (changed && threadIdx.x == 0) atomicOr(&a.ctl->cc_changed[round & 3], 1u);
 }
 
-__device__ void jump_phase(const CcArgs &a) {
+// Every vertex points at its root.
+__device__ void compress(const CcArgs &a) {
     for (int64_t v = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; v < a.nv;
          v += (int64_t)gridDim.x * blockDim.x) {
-        int32_t p = __ldcg(a.label + v);
+        const int32_t p = __ldcg(a.label + v);
         if (p == v) continue;
-        int32_t r = find_root(a.label, p);
+        const int32_t r = find_root(a.label, p);
         if (r != p) a.label[v] = r;
     }
 }
 
+// Hooks every non-isolated vertex to its k-th neighbour.
+__device__ void hook_kth(const CcArgs &a, uint32_t k) {
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < a.n_active;
+         i += (int64_t)gridDim.x * blockDim.x) {
+        const uint32_t b = __ldg(a.aoff + i), e = __ldg(a.aoff + i + 1);
+        if (b + k < e) hook(a.label, __ldg(a.active + i), __ldg(a.col + b + k), a.ctl);
+    }
+}
+
+// Block 0: the most frequent root among CC_SAMPLES vertices spread over the
+// active list (ties go to the smaller root).
+__device__ void find_giant(const CcArgs &a) {
+    __shared__ int32_t roots[CC_SAMPLES];
+    __shared__ unsigned long long best;
+    if (threadIdx.x == 0) best = 0ull;
+    for (int s = threadIdx.x; s < CC_SAMPLES; s += blockDim.x) {
+        // Knuth's multiplicative hash of s spreads the samples
+        const uint64_t h = ((uint64_t)s * 2654435761ull) % (uint64_t)(a.n_active > 0 ? a.n_active : 1);
+        roots[s] = a.n_active > 0 ? __ldcg(a.label + __ldg(a.active + h)) : 0;
+    }
+    __syncthreads();
+    for (int s = threadIdx.x; s < CC_SAMPLES; s += blockDim.x) {
+        int c = 0;
+        for (int t = 0; t < CC_SAMPLES; ++t) c += roots[t] == roots[s];
+        atomicMax(&best, ((unsigned long long)c << 32) | (unsigned)(0x7fffffff - roots[s]));
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) a.ctl->cc_giant = 0x7fffffff - (int32_t)(best & 0xffffffffull);
+}
+
+// Vertices outside the largest component hook their remaining edges.
+__device__ void hook_rest(const CcArgs &a, int32_t giant, unsigned long long &linked) {
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < a.n_active;
+         i += (int64_t)gridDim.x * blockDim.x) {
+        const int32_t v = __ldg(a.active + i);
+        if (find_root(a.label, v) == giant) continue;
+        const uint32_t b = __ldg(a.aoff + i), e = __ldg(a.aoff + i + 1);
+        for (uint32_t k = b + 2; k < e; ++k) hook(a.label, v, __ldg(a.col + k), a.ctl);
+        linked += e > b + 2 ? e - b - 2 : 0u;
+    }
+}
+
 __global__ void __launch_bounds__(CC_BLOCK) k_cc_persistent(CcArgs a) {
-    __shared__ CcSmem sm;
     FlagBarrier bar{a.bar_flags, &a.ctl->bar_release, a.ctl, a.timeout_ns, 0u};
     for (int64_t v = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; v < a.nv;
          v += (int64_t)gridDim.x * blockDim.x)
         a.label[v] = (int32_t)v;
-    if (blockIdx.x == 0 && threadIdx.x < 4) a.ctl->cc_changed[threadIdx.x] = 0u;
     if (!flag_barrier(bar)) return;
-    for (int round = 0;; ++round) {
-        if (blockIdx.x == 0 && threadIdx.x == 0) a.ctl->cc_changed[(round + 2) & 3] = 0u;
-        hook_phase(a, round, sm);
+    for (uint32_t k = 0; k < 2; ++k) {
+        hook_kth(a, k);
         if (!flag_barrier(bar)) return;
-        if (threadIdx.x == 0) sm.changed = ld_relaxed_u32(&a.ctl->cc_changed[round & 3]) != 0;
-        __syncthreads();
-        if (!sm.changed) {
-            if (blockIdx.x == 0 && threadIdx.x == 0) a.ctl->levels_run = round + 1;
-            return;
-        }
-        jump_phase(a);
+        compress(a);
         if (!flag_barrier(bar)) return;
+    }
+    if (blockIdx.x == 0) find_giant(a);
+    if (!flag_barrier(bar)) return;
+    const int32_t giant = ld_relaxed_u32((const unsigned int *)&a.ctl->cc_giant);
+    unsigned long long linked = 0;
+    hook_rest(a, giant, linked);
+    if (!flag_barrier(bar)) return;
+    compress(a);
+    linked = warp_sum(linked);
+    if ((threadIdx.x & 31) == 0 && linked) atomicAdd(&a.stats->edges_examined[0], linked);
+    if (blockIdx.x == 0 && threadIdx.x == 0) {
+        a.ctl->levels_run = 1;
+        a.stats->levels = 1;
     }
 }
 
@@ -123,17 +151,13 @@ __global__ void __launch_bounds__(CC_BLOCK) k_cc_persistent(CcArgs a) {
 grx_status grx_cc_launch(grx_graph *g, int32_t *label, const grx_opts *o, cudaStream_t s) {
     CcArgs a;
     a.nv = g->nv;
-    a.ne = g->ne;
     a.col = g->col;
     a.active = g->active;
     a.aoff = g->aoff;
-    a.tiles = nullptr;
-    if (g->ne > 0) {
-        grx_status st = grx_edge_tiles(g, CC_TILE, s, &a.tiles);
-        if (st != GRX_OK) return st;
-    }
+    a.n_active = g->n_active;
     a.label = label;
     a.ctl = g->ctl;
+    a.stats = g->stats;
     a.bar_flags = g->bar_flags;
     a.timeout_ns = grx_timeout_ns(o);
     static int per_sm = -1;
@@ -146,6 +170,8 @@ grx_status grx_cc_launch(grx_graph *g, int32_t *label, const grx_opts *o, cudaSt
     int blocks = o->grid_blocks > 0 && o->grid_blocks < max_grid ? o->grid_blocks : max_grid;
     GRX_CUDA(cudaMemsetAsync(g->bar_flags, 0, sizeof(unsigned int) * (size_t)blocks, s));
     GRX_CUDA(cudaMemsetAsync(&g->ctl->bar_release, 0, sizeof(unsigned int), s));
+    GRX_CUDA(cudaMemsetAsync(&g->stats->levels, 0, sizeof(int32_t), s));
+    GRX_CUDA(cudaMemsetAsync(&g->stats->edges_examined[0], 0, sizeof(unsigned long long), s));
     void *args[] = {(void *)&a};
     GRX_CUDA(cudaLaunchCooperativeKernel((const void *)k_cc_persistent, dim3(blocks), dim3(CC_BLOCK),
                                          args, 0, s));

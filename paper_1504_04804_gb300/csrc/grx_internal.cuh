@@ -31,7 +31,8 @@ struct alignas(128) TravCtl {
     unsigned long long cpack;        // BFS bitmap->queue compaction counter (count << 32 | edges)
     unsigned int ms_grid;            // multi-source BFS: grid of the last traversal
     unsigned int ms_done;            // ... blocks that completed its final pass
-    unsigned int pad0[14];
+    int cc_giant;                    // CC: root of the sampled largest component
+    unsigned int pad0[13];
     unsigned int bar_count;          // grid barrier arrivals
     unsigned int pad1[31];
     unsigned int bar_gen;            // grid barrier generation

@@ -451,7 +451,7 @@ __device__ void ms_compact(const MsArgs<OffT> &a, const MsState &st) {
 
 // Per-thread counters of the next frontier found by a pull level.
 struct MsCounts {
-    unsigned long long q, T, pairs, gathered;
+    unsigned long long q, T, pairs, gathered, rows;
 };
 
 // A pull-level row v gets its new lanes nw: seen, the history slot and the
@@ -494,6 +494,7 @@ __device__ void ms_pull(const MsArgs<OffT> &a, const MsState &st, MsPullSmem &p,
         if (threadIdx.x == 0) {
             a.fix[tile] = -1;
             s_open = 0;
+            if (STATS) c.rows += (unsigned long long)n;
         }
         __syncthreads();
         // a run of MS_PITEMS consecutive edges per thread: rows first, then
@@ -691,18 +692,23 @@ __global__ void __launch_bounds__(MS_BLOCK, GRX_MS_MIN_BLOCKS) k_msbfs_persisten
         } else if (op == MOP_FLUSH) {
             ms_flush<OffT>(a, MS_HSLOTS, st.slot_depth, false);
         } else {
-            MsCounts c = {0ull, 0ull, 0ull, 0ull};
+            MsCounts c = {0ull, 0ull, 0ull, 0ull, 0ull};
             if (op == MOP_PULL) ms_pull<OffT, STATS>(a, st, sm.p, c);
             else ms_pull_fixup<OffT>(a, st, c);
             c.q = warp_sum(c.q);
             c.T = warp_sum(c.T);
             c.pairs = warp_sum(c.pairs);
-            if (STATS) c.gathered = warp_sum(c.gathered);
+            if (STATS) {
+                c.gathered = warp_sum(c.gathered);
+                c.rows = warp_sum(c.rows);
+            }
             if ((threadIdx.x & 31) == 0) {
                 if (c.q) atomicAdd(&a.ctl->qpack[(L + 1) & 3], (c.q << 32) | c.T);
                 if (c.pairs) atomicAdd(&a.ctl->pairs[(L + 1) & 3], c.pairs);
                 if (STATS && c.gathered && L < GRX_MAX_LEVELS_STATS)
                     atomicAdd(&a.stats->edges_examined[L], c.gathered);
+                if (STATS && c.rows && L < GRX_MAX_LEVELS_STATS)
+                    atomicAdd(&a.stats->vertices_scanned[L], c.rows);   // rows of the tiles not skipped
             }
         }
         if (!flag_barrier(bar)) return;
