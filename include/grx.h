@@ -132,6 +132,14 @@ typedef struct {
                              in a second pass (no per-edge atomic with a
                              return value); 0 = 1/8, < 0 = never.  Results do
                              not depend on it. */
+    unsigned int sssp_delta; /* SSSP near-far band width (Davidson et al.'s
+                             near-far priority split of the frontier): a
+                             round relaxes only vertices closer than the
+                             current threshold, the others wait in a far pile
+                             until the threshold advances to the pile's
+                             smallest distance + delta.  0 = no bands (plain
+                             label-correcting rounds).  Results do not depend
+                             on it. */
 } grx_opts;
 
 /* Library defaults: AUTO direction, alpha 0.01, beta 0.1 (Sec. 6.1's values

@@ -32,7 +32,9 @@ struct alignas(128) TravCtl {
     unsigned int ms_grid;            // multi-source BFS: grid of the last traversal
     unsigned int ms_done;            // ... blocks that completed its final pass
     int cc_giant;                    // CC: root of the sampled largest component
-    unsigned int pad0[13];
+    unsigned int farcnt[2];          // SSSP near-far: far pile lengths (ping-pong)
+    unsigned int farmin[2];          // SSSP near-far: smallest distance in the far pile (by pile)
+    unsigned int pad0[9];
     unsigned int bar_count;          // grid barrier arrivals
     unsigned int pad1[31];
     unsigned int bar_gen;            // grid barrier generation

@@ -19,6 +19,13 @@
 //    changed vertices in vertex order and clears the bitmap.  A lane reduces
 //    only when its proposal beats the current distance read from L2, so every
 //    marked vertex did improve in the round and every improvement is marked.
+// Near-far bands (Davidson et al.'s near-far split, opt-in with delta > 0):
+// an improved vertex joins the next frontier only if its distance is below
+// the threshold, else it waits once in a far pile (a bitmap keeps it unique).
+// When the frontier runs dry, the threshold moves to the pile's smallest
+// distance + delta and the pile's vertices below it form the next frontier;
+// entries below the old threshold were relaxed since and are dropped.  High-
+// diameter weighted graphs then relax far fewer edges more than once.
 // Rounds and phases are separated by the bounded grid barrier.
 #include "grx_internal.cuh"
 
@@ -40,6 +47,9 @@ struct SsspArgs {
     uint32_t *dist;
     int32_t *stamp;
     uint32_t *cbits;                         // changed bitmap of reduction rounds
+    uint32_t *fbits;                         // near-far: far pile membership
+    int32_t *far[2];                         // near-far: far piles (ping-pong)
+    uint32_t delta;                          // near-far band width (0 = no bands)
     int32_t *Q[3];
     uint32_t *E[3];
     OffT *R[3];
@@ -51,12 +61,18 @@ struct SsspArgs {
     int32_t src;
 };
 
+enum { SOP_RELAX, SOP_FINAL, SOP_FARMIN, SOP_FARSPLIT };
+
 struct SsState {
     int L;
-    int phase;
+    int op;
     int bmp;
     int done;
+    int fsel;                                // current far pile
     uint32_t q, T;
+    uint32_t thr;                            // near-far threshold (UINT32_MAX: no bands)
+    uint32_t oldthr;                         // threshold before the last advance
+    uint32_t nfar;                           // current far pile length
 };
 
 template <typename OffT>
@@ -74,6 +90,16 @@ union SsWarpSmem {
 template <typename OffT>
 __device__ __forceinline__ void ss_set_kind(const SsspArgs<OffT> &a, SsState &s) {
     s.bmp = s.T >= a.bmp_min_T;
+}
+
+// v improved to a distance at or above the threshold: into the far pile once.
+template <typename OffT>
+__device__ __forceinline__ void far_push(const SsspArgs<OffT> &a, const SsState &st, int32_t v) {
+    const uint32_t bit = 1u << (v & 31);
+    if (!(atomicOr(a.fbits + (v >> 5), bit) & bit)) {
+        const unsigned int pos = atomicAdd(&a.ctl->farcnt[st.fsel], 1u);
+        a.far[st.fsel][pos] = v;
+    }
 }
 
 // Phase 0 of round L: relax the edges of Q_L.
@@ -172,8 +198,11 @@ __device__ void relax_round(const SsspArgs<OffT> &a, const SsState &st, SsWarpSm
             }
             uint32_t queued = 0;
 #pragma unroll
-            for (int k = 0; k < SS_ITEMS; ++k)
-                if ((improved >> k & 1u) && atomicExch(a.stamp + v[k], L + 1) != L + 1) queued |= 1u << k;
+            for (int k = 0; k < SS_ITEMS; ++k) {
+                if (!(improved >> k & 1u)) continue;
+                if (nd[k] >= st.thr) far_push(a, st, v[k]);
+                else if (atomicExch(a.stamp + v[k], L + 1) != L + 1) queued |= 1u << k;
+            }
             uint32_t deg[SS_ITEMS];
             OffT rb[SS_ITEMS];
             uint32_t app = 0;
@@ -222,7 +251,9 @@ __device__ void changed_to_queue(const SsspArgs<OffT> &a, const SsState &st, uin
                 v[k] = i < n ? (int32_t)(sc * 1024 + list[i]) : 0;
                 rb[k] = 0;
                 deg[k] = 0;
-                if (i < n) {
+                if (i < n && __ldcg(a.dist + v[k]) >= st.thr) {
+                    far_push(a, st, v[k]);
+                } else if (i < n) {
                     rb[k] = __ldg(a.ro + v[k]);
                     deg[k] = (uint32_t)(__ldg(a.ro + v[k] + 1) - rb[k]);
                     if (deg[k]) app |= 1u << k;
@@ -234,6 +265,110 @@ __device__ void changed_to_queue(const SsspArgs<OffT> &a, const SsState &st, uin
     }
 }
 
+// Band advance, phase 1: the smallest distance in the far pile.  The minimum
+// of pile f goes to farmin[f]; farmin[f ^ 1], read by every block after the
+// previous advance's barrier, is reset here for the next advance.
+template <typename OffT>
+__device__ void far_min(const SsspArgs<OffT> &a, const SsState &st) {
+    if (blockIdx.x == 0 && threadIdx.x == 0) {
+        a.ctl->farcnt[st.fsel ^ 1] = 0u;
+        a.ctl->farmin[st.fsel ^ 1] = 0xffffffffu;
+    }
+    const int32_t *F = a.far[st.fsel];
+    uint32_t m = 0xffffffffu;
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < (int64_t)st.nfar;
+         i += (int64_t)gridDim.x * blockDim.x) {
+        const uint32_t d = __ldcg(a.dist + __ldcg(F + i));
+        if (d >= st.thr) m = min(m, d);          // below the threshold: relaxed since, stale
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) m = min(m, __shfl_xor_sync(GRX_FULL_MASK, m, o));
+    if ((threadIdx.x & 31) == 0 && m != 0xffffffffu) atomicMin(&a.ctl->farmin[st.fsel], m);
+}
+
+// Band advance, phase 2 (threshold already raised): far vertices below the
+// new threshold form Q_L, the others move to the other pile, stale ones drop.
+template <typename OffT>
+__device__ void far_split(const SsspArgs<OffT> &a, const SsState &st) {
+    const int L = st.L;
+    int32_t *Qv = pick3(a.Q[0], a.Q[1], a.Q[2], L % 3);
+    uint32_t *Qe = pick3(a.E[0], a.E[1], a.E[2], L % 3);
+    OffT *Qr = pick3(a.R[0], a.R[1], a.R[2], L % 3);
+    const int32_t *F = a.far[st.fsel];
+    int32_t *G = a.far[st.fsel ^ 1];
+    const int64_t span = ((int64_t)st.nfar + 31) & ~(int64_t)31;
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < span;
+         i += (int64_t)gridDim.x * blockDim.x) {
+        int32_t v[1] = {0};
+        uint32_t deg[1] = {0};
+        OffT rb[1] = {0};
+        uint32_t app = 0;
+        if (i < (int64_t)st.nfar) {
+            v[0] = __ldcg(F + i);
+            const uint32_t d = __ldcg(a.dist + v[0]);
+            if (d >= st.thr) {                                   // still far
+                const unsigned int pos = atomicAdd(&a.ctl->farcnt[st.fsel ^ 1], 1u);
+                G[pos] = v[0];
+            } else {
+                atomicAnd(a.fbits + (v[0] >> 5), ~(1u << (v[0] & 31)));
+                if (d >= st.oldthr) {                            // first reached the band now
+                    rb[0] = __ldg(a.ro + v[0]);
+                    deg[0] = (uint32_t)(__ldg(a.ro + v[0] + 1) - rb[0]);
+                    if (deg[0]) app = 1;
+                }
+            }
+        }
+        warp_append_items<1, OffT>(v, deg, rb, app, Qv, Qe, Qr, &a.ctl->qpack[L & 3]);
+    }
+}
+
+// State of the next phase.
+template <typename OffT>
+__device__ SsState ss_next(const SsspArgs<OffT> &a, const SsState &st, bool stats) {
+    SsState ns = st;
+    if (st.op == SOP_RELAX && st.bmp) {
+        ns.op = SOP_FINAL;
+        return ns;
+    }
+    if (st.op == SOP_FARMIN) {
+        const uint32_t m = ld_relaxed_u32(&a.ctl->farmin[st.fsel]);
+        ns.op = SOP_FARSPLIT;
+        ns.oldthr = st.thr;
+        ns.thr = m == 0xffffffffu ? st.thr
+                                  : (m > 0xffffffffu - a.delta ? 0xffffffffu : m + a.delta);
+        if (m == 0xffffffffu) ns.thr = 0xffffffffu;              // every entry stale: one last split
+        return ns;
+    }
+    uint32_t q, T;
+    int L;
+    if (st.op == SOP_FARSPLIT) {                                 // Q_L came from the far pile
+        L = st.L;
+        ns.fsel = st.fsel ^ 1;
+        ns.nfar = ld_relaxed_u32(&a.ctl->farcnt[ns.fsel]);
+    } else {                                                     // end of round st.L
+        L = st.L + 1;
+        ns.nfar = ld_relaxed_u32(&a.ctl->farcnt[st.fsel]);
+    }
+    const unsigned long long pk = ld_relaxed_u64(&a.ctl->qpack[L & 3]);
+    q = (uint32_t)(pk >> 32);
+    T = (uint32_t)pk;
+    if (stats && blockIdx.x == 0 && st.op != SOP_FARSPLIT && st.L < GRX_MAX_LEVELS_STATS)
+        a.stats->discovered[st.L] = q;
+    ns.L = L;
+    ns.q = q;
+    ns.T = T;
+    if (q > 0) {
+        ns.op = SOP_RELAX;
+        ss_set_kind(a, ns);
+    } else if (a.delta && ns.nfar > 0) {
+        ns.op = SOP_FARMIN;
+        ns.bmp = 0;
+    } else {
+        ns.done = 1;
+    }
+    return ns;
+}
+
 template <typename OffT, bool STATS>
 __global__ void __launch_bounds__(SS_BLOCK, 3) k_sssp_persistent(SsspArgs<OffT> a) {
     __shared__ SsState s_st;
@@ -242,12 +377,13 @@ __global__ void __launch_bounds__(SS_BLOCK, 3) k_sssp_persistent(SsspArgs<OffT> 
     FlagBarrier bar{a.bar_flags, &a.ctl->bar_release, a.ctl, a.timeout_ns, 0u};
     if (threadIdx.x == 0) {
         SsState s;
+        memset(&s, 0, sizeof s);
         const uint32_t deg = (uint32_t)(a.ro[a.src + 1] - a.ro[a.src]);
-        s.L = 0;
-        s.phase = 0;
+        s.op = SOP_RELAX;
         s.q = deg ? 1u : 0u;
         s.T = deg;
         s.done = deg == 0;
+        s.thr = a.delta ? a.delta : 0xffffffffu;
         ss_set_kind(a, s);
         s_st = s;
     }
@@ -256,7 +392,7 @@ __global__ void __launch_bounds__(SS_BLOCK, 3) k_sssp_persistent(SsspArgs<OffT> 
         const SsState st = s_st;
         if (st.done) break;
         const int L = st.L;
-        if (st.phase == 0 && blockIdx.x == 0 && threadIdx.x == 0) {
+        if (st.op == SOP_RELAX && blockIdx.x == 0 && threadIdx.x == 0) {
             a.ctl->qpack[(L + 2) & 3] = 0ull;
             if (STATS && L < GRX_MAX_LEVELS_STATS) {
                 a.stats->level_t0[L] = grx_globaltimer();
@@ -267,26 +403,13 @@ __global__ void __launch_bounds__(SS_BLOCK, 3) k_sssp_persistent(SsspArgs<OffT> 
                 a.stats->levels = L + 1;
             }
         }
-        if (st.phase == 1) changed_to_queue<OffT>(a, st, w.list);
+        if (st.op == SOP_FINAL) changed_to_queue<OffT>(a, st, w.list);
+        else if (st.op == SOP_FARMIN) far_min<OffT>(a, st);
+        else if (st.op == SOP_FARSPLIT) far_split<OffT>(a, st);
         else if (st.bmp) relax_round<OffT, true>(a, st, w);
         else relax_round<OffT, false>(a, st, w);
         if (!flag_barrier(bar)) return;
-        if (threadIdx.x == 0) {
-            SsState ns = st;
-            if (st.bmp && st.phase == 0) {
-                ns.phase = 1;
-            } else {
-                const unsigned long long pk = ld_relaxed_u64(&a.ctl->qpack[(L + 1) & 3]);
-                ns.L = L + 1;
-                ns.phase = 0;
-                ns.q = (uint32_t)(pk >> 32);
-                ns.T = (uint32_t)pk;
-                ns.done = ns.q == 0;
-                ss_set_kind(a, ns);
-                if (STATS && blockIdx.x == 0 && L < GRX_MAX_LEVELS_STATS) a.stats->discovered[L] = ns.q;
-            }
-            s_st = ns;
-        }
+        if (threadIdx.x == 0) s_st = ss_next(a, st, STATS);
         __syncthreads();
     }
     if (blockIdx.x == 0 && threadIdx.x == 0) {
@@ -306,6 +429,10 @@ __global__ void k_sssp_init(int32_t src, const OffT *ro, uint32_t *dist, int32_t
     R0[0] = b;
     ctl->qpack[0] = deg ? ((1ull << 32) | deg) : 0ull;
     for (int i = 1; i < 4; ++i) ctl->qpack[i] = 0ull;
+    ctl->farcnt[0] = 0u;
+    ctl->farcnt[1] = 0u;
+    ctl->farmin[0] = 0xffffffffu;
+    ctl->farmin[1] = 0xffffffffu;
     if (stats_on) stats->levels = 0;
 }
 
@@ -321,6 +448,10 @@ grx_status launch_typed(grx_graph *g, int32_t src, uint32_t *dist, const grx_opt
     a.dist = dist;
     a.stamp = g->stamp;
     a.cbits = g->fbits[0];
+    a.fbits = g->fbits[1];
+    a.far[0] = g->ulist[0];
+    a.far[1] = g->ulist[1];
+    a.delta = o->sssp_delta;
     for (int i = 0; i < 3; ++i) {
         a.Q[i] = g->qv[i];
         a.E[i] = g->qe[i];
@@ -366,6 +497,7 @@ grx_status grx_sssp_launch(grx_graph *g, int32_t src, uint32_t *dist, const grx_
     GRX_CUDA(cudaMemsetAsync(dist, 0xff, nv * 4, s));
     GRX_CUDA(cudaMemsetAsync(g->stamp, 0, nv * 4, s));
     GRX_CUDA(cudaMemsetAsync(g->fbits[0], 0, (size_t)g->words * 4, s));
+    if (o->sssp_delta) GRX_CUDA(cudaMemsetAsync(g->fbits[1], 0, (size_t)g->words * 4, s));
     if (o->collect_stats) GRX_CUDA(cudaMemsetAsync(g->stats, 0, sizeof(DevStats), s));
     if (g->off64)
         return o->collect_stats ? launch_typed<int64_t, true>(g, src, dist, o, s)

@@ -40,7 +40,8 @@ class grx_opts(ctypes.Structure):
                 ("block_threads", ctypes.c_int), ("timeout_s", ctypes.c_double),
                 ("collect_stats", ctypes.c_int), ("exact_fv", ctypes.c_int),
                 ("ev_begin", ctypes.c_void_p),
-                ("ev_end", ctypes.c_void_p), ("push_bitmap", ctypes.c_float)]
+                ("ev_end", ctypes.c_void_p), ("push_bitmap", ctypes.c_float),
+                ("sssp_delta", ctypes.c_uint)]
 
 
 class grx_trav_stats(ctypes.Structure):

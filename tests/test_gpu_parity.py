@@ -139,15 +139,16 @@ def test_bfs_small_grids(grx, loaded):
 
 @pytest.mark.parametrize("name", list(GRAPHS))
 @pytest.mark.parametrize("pb", list(PUSH_BITMAP))
-def test_sssp_matches_oracle(grx, loaded, name, pb):
+@pytest.mark.parametrize("delta", [0, 1, 7, 300])
+def test_sssp_matches_oracle(grx, loaded, name, pb, delta):
     g, dg = GRAPHS[name], loaded[name]
-    o = grx.opts(push_bitmap=PUSH_BITMAP[pb])
+    o = grx.opts(push_bitmap=PUSH_BITMAP[pb], sssp_delta=delta)
     for s in _sources(g, 3) + [g.nv - 1]:
         d = grx.sssp(dg, s, opts=o)
         grx.graph_status(dg)
         got = grx.as_uint32(d)
         want = oracle.sssp(g.row_offsets, g.col_indices, g.weights, s)
-        assert np.array_equal(got, want), (name, pb, s)
+        assert np.array_equal(got, want), (name, pb, delta, s)
 
 
 @pytest.mark.parametrize("name", list(GRAPHS))
@@ -213,8 +214,9 @@ def test_exhaustive_6_vertex_graphs_as_one_union(grx):
         for mode, pb in itertools.product((0, 1, 2), (0.0, 1e-9)):
             d = grx.bfs(du, s, opts=grx.opts(direction=mode, push_bitmap=pb)).cpu().numpy()
             assert np.array_equal(d, oracle.bfs(u.row_offsets, u.col_indices, s))
-        dist = grx.as_uint32(grx.sssp(du, s))
-        assert np.array_equal(dist, oracle.sssp(u.row_offsets, u.col_indices, u.weights, s))
+        for delta in (0, 2):
+            dist = grx.as_uint32(grx.sssp(du, s, opts=grx.opts(sssp_delta=delta)))
+            assert np.array_equal(dist, oracle.sssp(u.row_offsets, u.col_indices, u.weights, s))
 
 
 def test_graph_without_edges_and_isolated_source(grx):
