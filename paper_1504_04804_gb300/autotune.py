@@ -10,7 +10,8 @@ timings on a few seeded tuning sources:
 * alpha (push->pull) and beta (pull->push);
 * the persistent grid size (full occupancy or half of it), the load-balance
   knob that remains at run time -- edge tiles are balanced by construction,
-  and the per-lane / per-group widths are compile-time constants.
+  and the per-lane / per-group widths are compile-time constants;
+* for SSSP, the near-far band width delta (``tune_sssp_delta``).
 
 Results do not depend on the parameters (the tests check this); only the
 time does.  The choice is cached in a JSON file keyed by a fingerprint of the
@@ -113,6 +114,56 @@ def tune_bfs(g, row_offsets, n_sources: int = 8, seed: int = 2, reps: int = 2,
     grx.graph_status(g)
     res = {"alpha": kw["alpha"], "beta": kw["beta"], "exact_fv": kw["exact_fv"],
            "grid_blocks": kw.get("grid_blocks", 0), "ms": med, "tried": tried,
+           "seconds": time.time() - t0, "fingerprint": fp, "tuning_sources": sources}
+    if cache:
+        data = _load(cache)
+        data[fp] = res
+        _save(cache, data)
+    return dict(res, cached=False)
+
+
+DELTA_FACTORS = (0, 4, 16, 64, 256)
+
+
+def tune_sssp_delta(g, row_offsets, weights, n_sources: int = 2, seed: int = 3,
+                    cache: str | None = DEFAULT_CACHE, force: bool = False) -> dict:
+    """Near-far band width for SSSP on a loaded weighted graph: 0 (plain
+    label-correcting rounds) or the mean edge weight times 4, 16, 64 or 256
+    (Davidson et al. scale the band with the weights), whichever gives the
+    smallest total kernel time over the tuning sources.
+    Returns {"sssp_delta", "ms", "tried", "seconds", "fingerprint", "cached"}."""
+    import torch
+
+    from . import grx, inputs
+    w = weights.cpu().numpy() if hasattr(weights, "cpu") else np.asarray(weights)
+    fp = fingerprint(row_offsets) + f"_w{int(w.sum()) if w.size else 0}_sssp"
+    if cache and not force:
+        hit = _load(cache).get(fp)
+        if hit:
+            return dict(hit, cached=True)
+    t0 = time.time()
+    mean_w = max(1.0, float(w.mean())) if w.size else 1.0
+    sources = [int(s) for s in inputs.pick_sources(row_offsets, n_sources, seed)]
+    stream = torch.cuda.current_stream()
+    dist = torch.empty(g.nv, dtype=torch.int32, device=f"cuda:{g.device}")
+    best = None
+    for f in DELTA_FACTORS:
+        delta = int(min(f * mean_w, 2 ** 31))
+        o = grx.opts(sssp_delta=delta)
+        tot = 0.0
+        for s in sources:
+            grx.sssp(g, s, dist_out=dist, opts=o)          # warm
+            ev0 = torch.cuda.Event(enable_timing=True)
+            ev1 = torch.cuda.Event(enable_timing=True)
+            ev0.record(stream)
+            grx.sssp(g, s, dist_out=dist, opts=o)
+            ev1.record(stream)
+            ev1.synchronize()
+            tot += ev0.elapsed_time(ev1)
+        if best is None or tot < best[0]:
+            best = (tot, delta)
+    grx.graph_status(g)
+    res = {"sssp_delta": best[1], "ms": best[0] / len(sources), "tried": len(DELTA_FACTORS),
            "seconds": time.time() - t0, "fingerprint": fp, "tuning_sources": sources}
     if cache:
         data = _load(cache)

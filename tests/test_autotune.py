@@ -38,3 +38,24 @@ def test_tuned_parameters_keep_results_exact(tmp_path):
     for s in inputs.pick_sources(g.row_offsets, 4, seed=5):
         assert np.array_equal(grx.bfs(dg, int(s), opts=o).cpu().numpy(),
                               oracle.bfs(g.row_offsets, g.col_indices, int(s)))
+
+
+@pytest.mark.gpu
+def test_tuned_sssp_delta_keeps_distances_exact(tmp_path):
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_1504_04804_gb300 import build, grx
+    build.build()
+    g = inputs.grid_graph(64, 64, p_del=0.1, seed=64, wmax=1000, weight_seed=164)
+    dg = grx.load(g)
+    cache = os.path.join(tmp_path, "tune.json")
+    t = autotune.tune_sssp_delta(dg, g.row_offsets, g.weights, cache=cache)
+    mean_w = float(np.mean(g.weights))
+    assert not t["cached"] and t["tried"] == len(autotune.DELTA_FACTORS)
+    assert t["sssp_delta"] in [int(min(f * mean_w, 2 ** 31)) for f in autotune.DELTA_FACTORS]
+    assert autotune.tune_sssp_delta(dg, g.row_offsets, g.weights, cache=cache)["cached"]
+    o = grx.opts(sssp_delta=t["sssp_delta"])
+    for s in inputs.pick_sources(g.row_offsets, 4, seed=5):
+        assert np.array_equal(grx.as_uint32(grx.sssp(dg, int(s), opts=o)),
+                              oracle.sssp(g.row_offsets, g.col_indices, g.weights, int(s)))
