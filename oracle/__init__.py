@@ -16,6 +16,9 @@ marshals numpy arrays through ctypes.
 * ``pagerank`` -- float64 power iteration with dangling mass spread evenly,
                   exactly ``iters`` updates from r = 1/N (Algorithm 3 and the
                   normalised-with-compensation mode of Sec. 7).
+* ``bc``       -- Brandes' dependency accumulation in float64: forward BFS
+                  counting shortest paths (sigma), backward pass in reverse
+                  BFS order (Table 1's BC, McLaughlin and Bader's scheme).
 * ``check_bfs`` / ``check_sssp`` / ``check_cc`` -- invariant checkers that
   hold at any size.
 
@@ -68,6 +71,8 @@ def _load():
     lib.oracle_cc.restype = ctypes.c_int
     lib.oracle_pagerank.argtypes = [i64, p, p, ctypes.c_double, ctypes.c_int, p]
     lib.oracle_pagerank.restype = ctypes.c_int
+    lib.oracle_bc.argtypes = [i64, p, p, p, i64, p, p]
+    lib.oracle_bc.restype = ctypes.c_int
     lib.oracle_check_bfs.argtypes = [i64, p, p, ctypes.c_int32, p, p]
     lib.oracle_check_bfs.restype = ctypes.c_int64
     lib.oracle_check_sssp.argtypes = [i64, p, p, p, ctypes.c_int32, p]
@@ -132,6 +137,20 @@ def pagerank(row_offsets, col_indices, damping: float = 0.85, iters: int = 20) -
     if rc != 0:
         raise OracleError(f"oracle_pagerank failed ({rc})")
     return rank
+
+
+def bc(row_offsets, col_indices, srcs, want_sigma: bool = False):
+    """Sum over ``srcs`` of Brandes' dependencies (float64 [nv]); with
+    ``want_sigma`` also the shortest-path counts of the last source."""
+    nv, ro, col = _csr(row_offsets, col_indices)
+    s = np.ascontiguousarray(np.atleast_1d(np.asarray(srcs, dtype=np.int32)))
+    out = np.empty(nv, dtype=np.float64)
+    sig = np.empty(nv, dtype=np.float64) if want_sigma else None
+    rc = _load().oracle_bc(nv, _ptr(ro), _ptr(col), _ptr(s), int(s.shape[0]), _ptr(out),
+                           None if sig is None else _ptr(sig))
+    if rc != 0:
+        raise OracleError(f"oracle_bc failed ({rc})")
+    return (out, sig) if want_sigma else out
 
 
 def check_bfs(row_offsets, col_indices, src: int, depth, parent=None) -> int:

@@ -207,6 +207,79 @@ int oracle_pagerank(int64_t nv, const int64_t *row_offsets, const int32_t *col_i
 }
 
 /* ------------------------------------------------------------------------ */
+/* Betweenness centrality.  Table 1 (Sec. 4) lists BC as a forward traversal */
+/* plus a backward pass over the same levels (W = 2|E|, S ~ D/2), the GPU    */
+/* scheme of McLaughlin and Bader (Sec. 2), which computes Brandes'          */
+/* dependencies.  For a source s on the undirected graph:                    */
+/*   sigma[v]  = number of shortest s-v paths (sigma[s] = 1);                */
+/*   delta[v]  = sum over t != s, v of sigma_st(v) / sigma_st, obtained by   */
+/*               delta[v] = sum over neighbours w one level deeper of        */
+/*                          sigma[v] / sigma[w] * (1 + delta[w]),            */
+/*               processing vertices in non-increasing distance from s.      */
+/* bc[v] is the sum of delta over the given sources (the source itself gets  */
+/* nothing from its own traversal); ordered pairs, so the all-sources sum on */
+/* an undirected graph counts each unordered pair twice.  Everything is      */
+/* float64.  sigma_last (optional) receives sigma of the last source, 0 for  */
+/* unreached vertices.                                                       */
+/* ------------------------------------------------------------------------ */
+int oracle_bc(int64_t nv, const int64_t *row_offsets, const int32_t *col_indices,
+              const int32_t *srcs, int64_t n_srcs, double *bc, double *sigma_last)
+{
+    if (nv <= 0 || !row_offsets || !bc || n_srcs < 0 || (n_srcs > 0 && !srcs)) return OR_EINVAL;
+    for (int64_t i = 0; i < n_srcs; ++i)
+        if (srcs[i] < 0 || (int64_t)srcs[i] >= nv) return OR_EINVAL;
+    int32_t *order = (int32_t *)malloc(sizeof(int32_t) * (size_t)nv);
+    int32_t *dist = (int32_t *)malloc(sizeof(int32_t) * (size_t)nv);
+    double *sigma = (double *)malloc(sizeof(double) * (size_t)nv);
+    double *delta = (double *)malloc(sizeof(double) * (size_t)nv);
+    if (!order || !dist || !sigma || !delta) {
+        free(order); free(dist); free(sigma); free(delta);
+        return OR_ENOMEM;
+    }
+    for (int64_t v = 0; v < nv; ++v) bc[v] = 0.0;
+    for (int64_t i = 0; i < n_srcs; ++i) {
+        const int32_t s = srcs[i];
+        for (int64_t v = 0; v < nv; ++v) {
+            dist[v] = -1;
+            sigma[v] = 0.0;
+            delta[v] = 0.0;
+        }
+        /* forward: BFS in FIFO order; order[] lists vertices by distance */
+        int64_t head = 0, tail = 0;
+        dist[s] = 0;
+        sigma[s] = 1.0;
+        order[tail++] = s;
+        while (head < tail) {
+            const int32_t u = order[head++];
+            for (int64_t e = row_offsets[u]; e < row_offsets[u + 1]; ++e) {
+                const int32_t w = col_indices[e];
+                if (dist[w] < 0) {
+                    dist[w] = dist[u] + 1;
+                    order[tail++] = w;
+                }
+                if (dist[w] == dist[u] + 1) sigma[w] += sigma[u];
+            }
+        }
+        /* backward: vertices in reverse BFS order, each one's delta complete
+           before any neighbour one level closer to s reads it */
+        for (int64_t k = tail - 1; k >= 0; --k) {
+            const int32_t v = order[k];
+            double sum = 0.0;
+            for (int64_t e = row_offsets[v]; e < row_offsets[v + 1]; ++e) {
+                const int32_t w = col_indices[e];
+                if (dist[w] == dist[v] + 1) sum += sigma[v] / sigma[w] * (1.0 + delta[w]);
+            }
+            delta[v] = sum;
+            if (v != s) bc[v] += delta[v];
+        }
+        if (sigma_last && i == n_srcs - 1)
+            for (int64_t v = 0; v < nv; ++v) sigma_last[v] = sigma[v];
+    }
+    free(order); free(dist); free(sigma); free(delta);
+    return OR_OK;
+}
+
+/* ------------------------------------------------------------------------ */
 /* Invariant checkers.  These hold at any size, so they let a full-size run  */
 /* be checked where only sampled sources can be re-solved exactly.  Each     */
 /* returns the number of violations found (0 = valid), or a negative error.  */

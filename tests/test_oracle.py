@@ -363,3 +363,129 @@ def test_pick_sources_non_isolated_distinct():
     s = inputs.pick_sources(g.row_offsets, 16, seed=1)
     assert len(set(s.tolist())) == 16
     assert np.all(np.diff(g.row_offsets)[s] > 0)
+
+
+# ---- betweenness centrality (Table 1's BC; Brandes' dependencies)
+
+def _union_csr(n, masks, pairs):
+    """Disjoint union of small graphs (graph g owns vertices g*n .. g*n+n-1)."""
+    edges = []
+    for gi, mask in enumerate(masks):
+        edges += [(gi * n + a, gi * n + b) for pi, (a, b) in enumerate(pairs) if mask >> pi & 1]
+    return inputs.csr_from_edges(n * len(masks), edges)
+
+
+def _bc_by_matrix_powers(n, masks, pairs):
+    """Definition-level BC of every vertex over every source, per graph.
+    sigma_st = (A^k)[s,t] for k = d(s,t), since every walk of minimal length
+    is a shortest path; d(s,t) = first k with (A^k)[s,t] > 0.  Then
+    bc(v) = sum over s != v != t, d(s,v) + d(v,t) = d(s,t), of
+    sigma_sv * sigma_vt / sigma_st."""
+    m = len(masks)
+    A = np.zeros((m, n, n), dtype=np.int64)
+    for gi, mask in enumerate(masks):
+        for pi, (a, b) in enumerate(pairs):
+            if mask >> pi & 1:
+                A[gi, a, b] = A[gi, b, a] = 1
+    D = np.full((m, n, n), np.inf)
+    S = np.zeros((m, n, n))
+    D[:, np.arange(n), np.arange(n)] = 0
+    S[:, np.arange(n), np.arange(n)] = 1
+    P = np.broadcast_to(np.eye(n, dtype=np.int64), (m, n, n)).copy()
+    for k in range(1, n):
+        P = P @ A
+        new = np.isinf(D) & (P > 0)
+        D[new] = k
+        S[new] = P[new]
+    Dsv, Dvt, Dst = D[:, :, :, None], D[:, None, :, :], D[:, :, None, :]
+    on = np.isfinite(Dst) & (Dsv + Dvt == Dst)
+    idx = np.arange(n)
+    on &= (idx[:, None, None] != idx[None, :, None])          # v != s
+    on &= (idx[None, :, None] != idx[None, None, :])          # v != t
+    on &= (idx[:, None, None] != idx[None, None, :])          # t != s
+    frac = np.where(on, S[:, :, :, None] * S[:, None, :, :] / np.where(on, S[:, :, None, :], 1.0), 0.0)
+    return frac.sum(axis=(1, 3)), frac[:, 0, :, :].sum(axis=2)   # all sources; source 0 only
+
+
+def test_bc_exhaustive_5_vertices_matches_matrix_power_definition():
+    n = 5
+    pairs = list(itertools.combinations(range(n), 2))
+    masks = list(range(1 << len(pairs)))
+    g = _union_csr(n, masks, pairs)
+    want_all, want_src0 = _bc_by_matrix_powers(n, masks, pairs)
+    got_all = oracle.bc(g.row_offsets, g.col_indices, np.arange(g.nv))
+    np.testing.assert_allclose(got_all, want_all.reshape(-1), rtol=1e-12, atol=1e-12)
+    got_src0 = oracle.bc(g.row_offsets, g.col_indices, np.arange(0, g.nv, n))
+    np.testing.assert_allclose(got_src0, want_src0.reshape(-1), rtol=1e-12, atol=1e-12)
+
+
+def test_bc_random_7_vertex_graphs_match_matrix_power_definition():
+    n = 7
+    pairs = list(itertools.combinations(range(n), 2))
+    rng = np.random.default_rng(7)
+    masks = [int(x) for x in rng.integers(0, 1 << len(pairs), size=400)]
+    g = _union_csr(n, masks, pairs)
+    want_all, want_src0 = _bc_by_matrix_powers(n, masks, pairs)
+    np.testing.assert_allclose(oracle.bc(g.row_offsets, g.col_indices, np.arange(g.nv)),
+                               want_all.reshape(-1), rtol=1e-12, atol=1e-12)
+    np.testing.assert_allclose(oracle.bc(g.row_offsets, g.col_indices, np.arange(0, g.nv, n)),
+                               want_src0.reshape(-1), rtol=1e-12, atol=1e-12)
+
+
+def test_bc_closed_forms():
+    n = 31
+    path = inputs.csr_from_edges(n, [(i, i + 1) for i in range(n - 1)])
+    i = np.arange(n, dtype=np.float64)
+    # all ordered pairs: vertex i lies inside i * (n-1-i) unordered pairs
+    assert np.array_equal(oracle.bc(path.row_offsets, path.col_indices, np.arange(n)),
+                          2 * i * (n - 1 - i))
+    # from vertex 0: vertex i >= 1 lies on the paths to the n-1-i vertices beyond it
+    d0, sig = oracle.bc(path.row_offsets, path.col_indices, [0], want_sigma=True)
+    assert np.array_equal(d0, np.where(i >= 1, n - 1 - i, 0.0)) and np.all(sig == 1.0)
+    # star with L leaves: the centre is on every leaf-to-leaf path
+    L = 12
+    star = inputs.csr_from_edges(L + 1, [(0, k) for k in range(1, L + 1)])
+    b = oracle.bc(star.row_offsets, star.col_indices, np.arange(L + 1))
+    assert b[0] == L * (L - 1) and np.all(b[1:] == 0)
+    b1 = oracle.bc(star.row_offsets, star.col_indices, [3])
+    assert b1[0] == L - 1 and np.all(b1[1:] == 0)
+    # complete graph: no vertex is strictly inside a shortest path
+    K = 9
+    comp = inputs.csr_from_edges(K, list(itertools.combinations(range(K), 2)))
+    assert np.all(oracle.bc(comp.row_offsets, comp.col_indices, np.arange(K)) == 0)
+    # cycles: every vertex equal; the values sum to sum over ordered pairs of (d - 1)
+    for c in (10, 11):
+        cyc = inputs.csr_from_edges(c, [(k, (k + 1) % c) for k in range(c)])
+        b = oracle.bc(cyc.row_offsets, cyc.col_indices, np.arange(c))
+        k = np.arange(1, c)
+        total = c * np.minimum(k, c - k).astype(np.float64).__sub__(1).sum()
+        np.testing.assert_allclose(b, np.full(c, total / c), rtol=1e-13)
+    # full lattice: shortest-path counts from (x0, y0) are binomial coefficients
+    from math import comb
+    w, h = 9, 7
+    u, v = inputs.grid_edges(w, h, 0.0, seed=1)
+    ro, col = inputs.build_csr(w * h, u, v)
+    x0, y0 = 3, 2
+    _, sig = oracle.bc(ro, col, [y0 * w + x0], want_sigma=True)
+    want = [comb(abs(x - x0) + abs(y - y0), abs(x - x0)) for y in range(h) for x in range(w)]
+    assert np.array_equal(sig, np.array(want, dtype=np.float64))
+
+
+def test_bc_dependency_sum_identity_and_unreached():
+    """sum over v of delta_s(v) = sum over reached t != s of (d(s,t) - 1): each
+    shortest s-t path has d(s,t) - 1 interior vertices.  Checked against the
+    BFS oracle's distances on an R-MAT graph; vertices in other components and
+    the source get nothing."""
+    g = _rmat_small()
+    for s in inputs.pick_sources(g.row_offsets, 4, seed=2):
+        s = int(s)
+        delta = oracle.bc(g.row_offsets, g.col_indices, [s])
+        d = oracle.bfs(g.row_offsets, g.col_indices, s)
+        reached = d > 0
+        np.testing.assert_allclose(delta.sum(), float((d[reached] - 1).sum()), rtol=1e-12)
+        assert delta[s] == 0 and np.all(delta[d < 0] == 0) and np.all(delta >= 0)
+    two = inputs.csr_from_edges(6, [(0, 1), (1, 2), (3, 4), (4, 5)])
+    assert np.array_equal(oracle.bc(two.row_offsets, two.col_indices, [0]),
+                          np.array([0, 1, 0, 0, 0, 0], dtype=np.float64))
+    with pytest.raises(oracle.OracleError):
+        oracle.bc(two.row_offsets, two.col_indices, [6])
