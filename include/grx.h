@@ -176,6 +176,24 @@ grx_status sssp(grx_graph *g, int32_t src, uint32_t *dist_out,
 grx_status sssp_multi(grx_graph *g, const int32_t *srcs_host, int n, uint32_t *dist_out,
                       const grx_opts *opts, void *stream);
 
+/* bc -- Table 1 BC: Brandes' dependencies of each source, by a forward
+ * shortest-path-counting BFS and a backward pass over the same levels
+ * (McLaughlin and Bader's scheme, Sec. 2).  For source s,
+ *   delta_s(v) = sum over t != s, v of sigma_st(v) / sigma_st
+ * (sigma_st = number of shortest s-t paths, sigma_st(v) = those through v).
+ * bc_out: device float64[nv], overwritten with the sum of delta_s over the n
+ * sources in srcs_host (host array, n >= 1, duplicates allowed); the source
+ * itself gets nothing from its own traversal, unreached vertices nothing.
+ * Ordered pairs: summed over every source of an undirected graph each
+ * unordered pair counts twice.  sigma_out: NULL or device float64[nv], the
+ * shortest-path counts sigma_{s,v} of the last source (0 if unreached).
+ * The graph must be symmetric (undirected, as every graph of Sec. 7).
+ * Float64 arithmetic; reductions arrive in any order, so values match a
+ * sequential float64 sum to rounding.  Uses 16 bytes of workspace per
+ * vertex.  Bad source or NULL output -> GRX_EINVAL. */
+grx_status bc(grx_graph *g, const int32_t *srcs_host, int n, double *bc_out, double *sigma_out,
+              const grx_opts *opts, void *stream);
+
 /* cc -- Table 1 CC (Soman et al.'s hooking + pointer jumping).  label_out:
  * device int32[nv], the minimum vertex id of the vertex's component. */
 grx_status cc(grx_graph *g, int32_t *label_out, void *stream);

@@ -439,6 +439,29 @@ extern "C" grx_status cc(grx_graph *g, int32_t *label_out, void *stream) {
     return grx_cc_launch(g, label_out, &o, (cudaStream_t)stream);
 }
 
+extern "C" grx_status bc(grx_graph *g, const int32_t *srcs_host, int n, double *bc_out, double *sigma_out,
+                         const grx_opts *opts, void *stream) {
+    grx_status st = check_graph(g, "bc");
+    if (st) return st;
+    if (!srcs_host || n < 1) return grx_fail(GRX_EINVAL, "bc: need at least one source");
+    for (int i = 0; i < n; ++i)
+        if (srcs_host[i] < 0 || srcs_host[i] >= g->nv)
+            return grx_fail(GRX_EINVAL, "bc: source %d (index %d) out of range", srcs_host[i], i);
+    if (!bc_out) return grx_fail(GRX_EINVAL, "bc: bc_out is NULL");
+    grx_opts o;
+    grx_resolve_opts(opts, &o);
+    g->last_stream = stream;
+    cudaStream_t s = (cudaStream_t)stream;
+    if ((st = grx_ensure_workspace(g, s))) return st;
+    if (!g->bc_sigma) {
+        g->bc_sigma = (double *)grx_alloc(g, (size_t)g->nv * 8, s);
+        g->bc_acc = (double *)grx_alloc(g, (size_t)g->nv * 8, s);
+        if (!g->bc_sigma || !g->bc_acc)
+            return grx_fail(GRX_ENOMEM, "bc: workspace allocation failed (nv=%d)", g->nv);
+    }
+    return grx_bc_launch(g, srcs_host, n, bc_out, sigma_out, &o, s);
+}
+
 extern "C" grx_status pagerank(grx_graph *g, float damping, int iters, float *rank_out,
                                void *stream) {
     grx_status st = check_graph(g, "pagerank");

@@ -123,6 +123,8 @@ struct grx_graph {
     uint8_t *ms_sat;                 // multi-source BFS: per pull tile, all lanes seen
     uint32_t *ms_dist;               // batched SSSP, vertex-major [nv][64]
     int ms_ready;
+    // betweenness centrality (allocated on first use)
+    double *bc_sigma, *bc_acc;       // [nv] each: path counts; successor sums / coefficients
     // CUDA-graph level loop of bfs (GRX_LOOP_GRAPH), per parent flag
     cudaGraphExec_t bfs_gexec[2];
     void *bfs_gargs;                 // device copy of the call's arguments
@@ -168,6 +170,8 @@ grx_status grx_bfs_launch(grx_graph *g, int32_t src, int32_t *depth, int32_t *pa
 grx_status grx_sssp_launch(grx_graph *g, int32_t src, uint32_t *dist, const grx_opts *o,
                            cudaStream_t s);
 grx_status grx_cc_launch(grx_graph *g, int32_t *label, const grx_opts *o, cudaStream_t s);
+grx_status grx_bc_launch(grx_graph *g, const int32_t *srcs, int n, double *bc_out, double *sigma_out,
+                         const grx_opts *o, cudaStream_t s);
 grx_status grx_pr_launch(grx_graph *g, float damping, int iters, float *rank,
                          cudaStream_t s);
 

@@ -76,6 +76,7 @@ SIGNATURES = [
     ("bfs", _I, [_P, ctypes.c_int32, _P, _P, _P, _P]),
     ("sssp", _I, [_P, ctypes.c_int32, _P, _P, _P]),
     ("cc", _I, [_P, _P, _P]),
+    ("bc", _I, [_P, _P, _I, _P, _P, _P, _P]),
     ("pagerank", _I, [_P, ctypes.c_float, _I, _P, _P]),
     ("grx_pagerank_block", _I, [_P, _I]),
     ("grx_last_stats", _I, [_P, _P, _P]),
@@ -315,6 +316,20 @@ def sssp_multi(g: Graph, srcs, dist_out=None, opts: grx_opts | None = None, stre
                             ctypes.byref(opts) if opts is not None else None, _stream_ptr(stream)),
            "sssp_multi")
     return d[: n * g.nv].view(n, g.nv)
+
+
+def bc(g: Graph, srcs, bc_out=None, sigma_out=None, opts: grx_opts | None = None, stream=None,
+       want_sigma: bool = False):
+    """Sum over the sources of Brandes' dependencies, float64 tensor [nv];
+    with ``want_sigma`` (or ``sigma_out``) also the shortest-path counts of
+    the last source: returns (bc, sigma)."""
+    arr = np.ascontiguousarray(np.atleast_1d(np.asarray(srcs, dtype=np.int32)))
+    out = _out(bc_out, g.nv, torch.float64, g.device)
+    sig = _out(sigma_out, g.nv, torch.float64, g.device) if (want_sigma or sigma_out is not None) else None
+    _check(lib().bc(g.handle, arr.ctypes.data_as(ctypes.c_void_p), int(arr.shape[0]), out.data_ptr(),
+                    sig.data_ptr() if sig is not None else None,
+                    ctypes.byref(opts) if opts is not None else None, _stream_ptr(stream)), "bc")
+    return (out, sig) if sig is not None else out
 
 
 def cc(g: Graph, label_out=None, stream=None):

@@ -423,3 +423,66 @@ def test_int64_offsets_every_primitive(grx, name):
                                       oracle.sssp(g.row_offsets, g.col_indices, g.weights, s))
         b.close()
     grx.graph_status(dg)
+
+
+# ---- betweenness centrality: float64 sums of nonnegative terms, so the
+# relative error of each value is bounded by (levels + log2 terms) * 2^-53
+# times a small constant -- far below BC_TOL on these graphs (at most 3,000
+# levels); path counts are integers, exact below 2^53.
+BC_TOL = 1e-9
+
+
+@pytest.mark.parametrize("name", list(GRAPHS))
+def test_bc_single_sources_match_oracle(grx, loaded, name):
+    g, dg = GRAPHS[name], loaded[name]
+    for s in _sources(g, 3, seed=4) + [0, g.nv - 1]:
+        got, sig = grx.bc(dg, [s], want_sigma=True)
+        want, wsig = oracle.bc(g.row_offsets, g.col_indices, [s], want_sigma=True)
+        np.testing.assert_allclose(got.cpu().numpy(), want, rtol=BC_TOL, atol=0, err_msg=f"{name} {s}")
+        np.testing.assert_allclose(sig.cpu().numpy(), wsig, rtol=1e-12, atol=0, err_msg=f"{name} {s}")
+
+
+@pytest.mark.parametrize("name", list(GRAPHS))
+def test_bc_sums_over_sources_match_oracle(grx, loaded, name):
+    g, dg = GRAPHS[name], loaded[name]
+    srcs = _sources(g, 6, seed=5)
+    srcs += srcs[:2]                                     # duplicates count twice
+    got = grx.bc(dg, srcs).cpu().numpy()
+    np.testing.assert_allclose(got, oracle.bc(g.row_offsets, g.col_indices, srcs), rtol=BC_TOL, atol=0)
+
+
+def test_bc_every_source_of_every_5_vertex_graph(grx):
+    """All 1,024 labelled graphs on 5 vertices as one disjoint union, every
+    vertex a source; a seeded sample of 6-vertex graphs likewise."""
+    for n, count in ((5, None), (6, 400)):
+        pairs = list(itertools.combinations(range(n), 2))
+        masks = range(1 << len(pairs)) if count is None else \
+            np.random.default_rng(n).choice(1 << len(pairs), size=count, replace=False)
+        edges = []
+        for gi, mask in enumerate(masks):
+            edges += [(gi * n + a, gi * n + b) for pi, (a, b) in enumerate(pairs) if int(mask) >> pi & 1]
+        u = inputs.csr_from_edges(n * len(masks), edges)
+        du = grx.load(u, validate=True)
+        srcs = np.arange(u.nv)
+        np.testing.assert_allclose(grx.bc(du, srcs).cpu().numpy(),
+                                   oracle.bc(u.row_offsets, u.col_indices, srcs), rtol=BC_TOL, atol=0)
+
+
+def test_bc_int64_offsets_and_edge_cases(grx):
+    g = GRAPHS["grid64"]
+    dg = grx.load(g, validate=True, offsets64=True)
+    srcs = _sources(g, 3, seed=6)
+    got, sig = grx.bc(dg, srcs, want_sigma=True)
+    want, wsig = oracle.bc(g.row_offsets, g.col_indices, srcs, want_sigma=True)
+    np.testing.assert_allclose(got.cpu().numpy(), want, rtol=BC_TOL, atol=0)
+    np.testing.assert_allclose(sig.cpu().numpy(), wsig, rtol=1e-12, atol=0)
+    # isolated source, graph without edges, bad arguments
+    dd = grx.load(GRAPHS["disconnected"])
+    b, s = grx.bc(dd, [0], want_sigma=True)
+    assert np.all(b.cpu().numpy() == 0) and s.cpu().numpy()[0] == 1 and np.all(s.cpu().numpy()[1:] == 0)
+    de = grx.load(inputs.csr_from_edges(50, []))
+    assert np.all(grx.bc(de, [3, 4]).cpu().numpy() == 0)
+    with pytest.raises(RuntimeError):
+        grx.bc(dd, [40])
+    with pytest.raises(RuntimeError):
+        grx.bc(dd, [])
