@@ -102,6 +102,37 @@ def cc_bytes(nv: int, hooked: int, off_bytes: int) -> int:
     return hooked * 12 + 3 * nv * (off_bytes + 4) + 3 * nv * 8
 
 
+def bc_bytes(nv: int, v_r: int, e_r: int, e_dag: int, off_bytes: int) -> int:
+    """Betweenness centrality, one source: depth, sigma and acc initialised
+    (20 bytes per vertex); per reached vertex, forward row offsets 2o, level
+    list write and read 2(8+o), sigma 8 and depth claim 4, backward list
+    (8+o), sigma 8, coefficient 8 and the bc update 16; per reached edge,
+    in both passes, column and depth probe (8 + 8); per shortest-path DAG
+    edge, the sigma reduction 16 and the coefficient gather 8."""
+    o = off_bytes
+    return nv * 20 + v_r * (2 * o + 2 * (8 + o) + 12 + (8 + o) + 32) + e_r * 16 + e_dag * 24
+
+
+def dag_edges(ro_h, col_dev, depth_dev) -> int:
+    """Edges (u, w) with depth[w] = depth[u] + 1, counted on the device in
+    chunks of about 2^27 edges."""
+    import torch
+    nv = depth_dev.numel()
+    ro_d = torch.from_numpy(np.ascontiguousarray(ro_h, dtype=np.int64)).to(depth_dev.device)
+    deg_d = ro_d[1:] - ro_d[:-1]
+    total, v0 = 0, 0
+    while v0 < nv:
+        v1 = int(np.searchsorted(ro_h, ro_h[v0] + (1 << 27), side="right")) - 1
+        v1 = min(nv, max(v1, v0 + 1))
+        e0, e1 = int(ro_h[v0]), int(ro_h[v1])
+        if e1 > e0:
+            du = torch.repeat_interleave(depth_dev[v0:v1], deg_d[v0:v1], output_size=e1 - e0)
+            dw = depth_dev[col_dev[e0:e1].long()]
+            total += int(((du >= 0) & (dw == du + 1)).sum())
+        v0 = v1
+    return total
+
+
 # ---------------------------------------------------------------------------
 class ClockSampler:
     """nvidia-smi clock/throttle samples while the timed region runs."""
@@ -408,7 +439,8 @@ def main():
               f"roofline {achieved / peak:.4f}, e2e {e2e['value']:.1f} GTEPS", file=sys.stderr, flush=True)
     extra = {}
     if not args.no_extra:
-        extra = other_primitives(grx, g, srcs, nv, ne, off_bytes, deg_h, flush, stream, peak)
+        extra = other_primitives(grx, g, srcs, nv, ne, off_bytes, deg_h, flush, stream, peak,
+                                 ro_h=ro_h, col_dev=col)
     if not args.no_extra and args.serving_queries > 0:
         # serving: this graph plus two smaller resident R-MAT graphs
         sgraphs, sdeg, sro = {f"rmat{cfg['scale']}": g}, {}, {f"rmat{cfg['scale']}": ro_h}
@@ -619,8 +651,9 @@ def serving_bench(graphs: dict, degrees: dict, host_ro: dict, n_queries: int, se
                                   "best_p99_ms": tbest["p99_ms"] if tbest else None}}
 
 
-def other_primitives(grx, g, srcs, nv, ne, off_bytes, deg_h, flush, stream, peak):
-    """SSSP, CC and PageRank on the same resident graph (CUDA events)."""
+def other_primitives(grx, g, srcs, nv, ne, off_bytes, deg_h, flush, stream, peak, ro_h=None, col_dev=None):
+    """SSSP, CC, multi-source BFS/SSSP, PageRank and BC on the same resident
+    graph (CUDA events)."""
     import torch
     out = {}
 
@@ -685,6 +718,23 @@ def other_primitives(grx, g, srcs, nv, ne, off_bytes, deg_h, flush, stream, peak
     pb = pr_bytes(nv, ne, off_bytes, 20)
     out["pagerank"] = {"ms": ts, "iters": 20, "ms_per_iter": statistics.median(ts) / 20,
                        "roofline_frac": pb / (statistics.median(ts) / 1e3) / 1e9 / peak}
+    # betweenness centrality: one source per call, 4 sources
+    bco = torch.empty(nv, dtype=torch.float64, device=flush.device)
+    bbytes, bedges, dags = [], [], []
+    for s in srcs[:4]:
+        dep = grx.bfs(g, s)
+        reached = dep.cpu().numpy() >= 0
+        e_r = int(deg_h[reached].sum())
+        v_r = int(np.count_nonzero(reached & (deg_h > 0)))
+        e_dag = dag_edges(ro_h, col_dev, dep) if col_dev is not None else e_r // 2
+        dags.append(e_dag)
+        bedges.append(e_r)
+        bbytes.append(bc_bytes(nv, v_r, e_r, e_dag, off_bytes))
+    ts = timed(lambda i: grx.bc(g, [srcs[i % 4]], bc_out=bco), 4)
+    grx.graph_status(g)
+    out["bc"] = {"ms": ts, "gteps": sum(bedges) / (sum(ts) / 1e3) / 1e9, "dag_edges": dags,
+                 "roofline_frac": sum(bbytes) / (sum(ts) / 1e3) / 1e9 / peak,
+                 "note": "one source per call; GTEPS counts each reached edge once"}
     return out
 
 

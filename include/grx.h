@@ -189,8 +189,13 @@ grx_status sssp_multi(grx_graph *g, const int32_t *srcs_host, int n, uint32_t *d
  * shortest-path counts sigma_{s,v} of the last source (0 if unreached).
  * The graph must be symmetric (undirected, as every graph of Sec. 7).
  * Float64 arithmetic; reductions arrive in any order, so values match a
- * sequential float64 sum to rounding.  Uses 16 bytes of workspace per
- * vertex.  Bad source or NULL output -> GRX_EINVAL. */
+ * sequential float64 sum to rounding.  Forward levels with at least
+ * opts->push_bitmap * nv edges mark the next level in a bitmap instead of
+ * claiming vertices one by one (results do not depend on it).  Uses about
+ * 16 bytes of workspace per vertex.  With opts->collect_stats, grx_last_stats describes the last
+ * source's phases: forward levels (dir 0) then backward levels (dir 1),
+ * frontier = the level's vertices, edges_examined = their edges.
+ * Bad source or NULL output -> GRX_EINVAL. */
 grx_status bc(grx_graph *g, const int32_t *srcs_host, int n, double *bc_out, double *sigma_out,
               const grx_opts *opts, void *stream);
 

@@ -456,7 +456,8 @@ extern "C" grx_status bc(grx_graph *g, const int32_t *srcs_host, int n, double *
     if (!g->bc_sigma) {
         g->bc_sigma = (double *)grx_alloc(g, (size_t)g->nv * 8, s);
         g->bc_acc = (double *)grx_alloc(g, (size_t)g->nv * 8, s);
-        if (!g->bc_sigma || !g->bc_acc)
+        g->bc_code = (uint32_t *)grx_alloc(g, (size_t)g->words * 8, s);
+        if (!g->bc_sigma || !g->bc_acc || !g->bc_code)
             return grx_fail(GRX_ENOMEM, "bc: workspace allocation failed (nv=%d)", g->nv);
     }
     return grx_bc_launch(g, srcs_host, n, bc_out, sigma_out, &o, s);

@@ -34,7 +34,8 @@ struct alignas(128) TravCtl {
     int cc_giant;                    // CC: root of the sampled largest component
     unsigned int farcnt[2];          // SSSP near-far: far pile lengths (ping-pong)
     unsigned int farmin[2];          // SSSP near-far: smallest distance in the far pile (by pile)
-    unsigned int pad0[9];
+    unsigned int bcfix[3];           // BC backward: rows finished after the barrier, by level mod 3
+    unsigned int pad0[6];
     unsigned int bar_count;          // grid barrier arrivals
     unsigned int pad1[31];
     unsigned int bar_gen;            // grid barrier generation
@@ -125,6 +126,7 @@ struct grx_graph {
     int ms_ready;
     // betweenness centrality (allocated on first use)
     double *bc_sigma, *bc_acc;       // [nv] each: path counts; successor sums / coefficients
+    uint32_t *bc_code;               // [2 * words]: 2-bit level codes
     // CUDA-graph level loop of bfs (GRX_LOOP_GRAPH), per parent flag
     cudaGraphExec_t bfs_gexec[2];
     void *bfs_gargs;                 // device copy of the call's arguments

@@ -433,10 +433,12 @@ BC_TOL = 1e-9
 
 
 @pytest.mark.parametrize("name", list(GRAPHS))
-def test_bc_single_sources_match_oracle(grx, loaded, name):
+@pytest.mark.parametrize("pb", list(PUSH_BITMAP))
+def test_bc_single_sources_match_oracle(grx, loaded, name, pb):
     g, dg = GRAPHS[name], loaded[name]
+    o = grx.opts(push_bitmap=PUSH_BITMAP[pb])
     for s in _sources(g, 3, seed=4) + [0, g.nv - 1]:
-        got, sig = grx.bc(dg, [s], want_sigma=True)
+        got, sig = grx.bc(dg, [s], want_sigma=True, opts=o)
         want, wsig = oracle.bc(g.row_offsets, g.col_indices, [s], want_sigma=True)
         np.testing.assert_allclose(got.cpu().numpy(), want, rtol=BC_TOL, atol=0, err_msg=f"{name} {s}")
         np.testing.assert_allclose(sig.cpu().numpy(), wsig, rtol=1e-12, atol=0, err_msg=f"{name} {s}")
