@@ -103,14 +103,15 @@ def cc_bytes(nv: int, hooked: int, off_bytes: int) -> int:
 
 
 def bc_bytes(nv: int, v_r: int, e_r: int, e_dag: int, off_bytes: int) -> int:
-    """Betweenness centrality, one source: depth, sigma and acc initialised
-    (20 bytes per vertex); per reached vertex, forward row offsets 2o, level
-    list write and read 2(8+o), sigma 8 and depth claim 4, backward list
-    (8+o), sigma 8, coefficient 8 and the bc update 16; per reached edge,
-    in both passes, column and depth probe (8 + 8); per shortest-path DAG
-    edge, the sigma reduction 16 and the coefficient gather 8."""
+    """Betweenness centrality, one source: sigma and acc initialised (16
+    bytes per vertex), 2-bit level codes and the next-level bitmap (3 bits);
+    per reached vertex, forward row offsets 2o, level list write and read
+    2(8+o), sigma 8 and the code update 4, backward list (8+o), sigma 8,
+    coefficient 8 and the bc update 16; per reached edge, in both passes,
+    column and level-code word (8 + 8); per shortest-path DAG edge, the
+    sigma reduction 16 and the coefficient gather 8."""
     o = off_bytes
-    return nv * 20 + v_r * (2 * o + 2 * (8 + o) + 12 + (8 + o) + 32) + e_r * 16 + e_dag * 24
+    return nv * 16 + (3 * nv) // 8 + v_r * (2 * o + 2 * (8 + o) + 12 + (8 + o) + 32) + e_r * 16 + e_dag * 24
 
 
 def dag_edges(ro_h, col_dev, depth_dev) -> int:
