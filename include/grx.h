@@ -191,7 +191,12 @@ grx_status sssp_multi(grx_graph *g, const int32_t *srcs_host, int n, uint32_t *d
  * Float64 arithmetic; reductions arrive in any order, so values match a
  * sequential float64 sum to rounding.  Forward levels with at least
  * opts->push_bitmap * nv edges mark the next level in a bitmap instead of
- * claiming vertices one by one (results do not depend on it).  Uses about
+ * claiming vertices one by one (results do not depend on it).
+ * opts->direction: GRX_DIR_AUTO picks per level by edge counts -- a forward
+ * level is a pull over the unreached vertices when they have less than a
+ * quarter of the frontier's edges, a backward level pushes from the level below when that
+ * one has fewer edges; GRX_DIR_PUSH keeps forward push / backward pull,
+ * GRX_DIR_PULL the other way round (after the source level).  Uses about
  * 16 bytes of workspace per vertex.  With opts->collect_stats, grx_last_stats describes the last
  * source's phases: forward levels (dir 0) then backward levels (dir 1),
  * frontier = the level's vertices, edges_examined = their edges.

@@ -31,6 +31,16 @@
 //    reductions), the tile holding its last edge lists v, and a short phase
 //    after the barrier finishes the listed vertices.  The deepest level has
 //    no successors: coef = 1 / sigma, delta = 0.
+//  * Direction per level (the paper's direction-optimising idea, Sec. 6.1,
+//    carried over to both sweeps, by edge counts the level lists provide):
+//    a forward level whose frontier has more than four times the edges of
+//    all still-unreached vertices together is a pull instead -- every unreached non-isolated
+//    vertex sums sigma over its neighbours at depth d (all of them: no early
+//    exit, sigma needs every parent) and joins level d + 1 if that sum is
+//    nonzero; a backward level whose rows hold more edges than the level
+//    below it is a push instead -- each vertex w of level k + 1 adds coef[w]
+//    into acc[v] of its neighbours at depth k (float64 reductions), and a
+//    second phase finishes level k's vertices.
 // One persistent cooperative kernel; phases separated by the bounded grid
 // barrier.  Float64 throughout: path counts are exact integers below 2^53,
 // and sums differ from a sequential order only in the last bits.
@@ -38,16 +48,27 @@
 
 namespace {
 
+#ifndef GRX_BC_MIN_BLOCKS
+#define GRX_BC_MIN_BLOCKS 3                 // resident blocks per SM (register cap)
+#endif
 constexpr int BC_BLOCK = 256;
 constexpr int BC_WARPS = BC_BLOCK / 32;
 constexpr int BC_ITEMS = 8;
 constexpr int BC_WTILE = 32 * BC_ITEMS;
 constexpr int BC_RPL = 4;                  // finalize: vertices per lane per round
+// A forward pull reads every edge of every unreached vertex (no early exit)
+// with a row per lane; measured on GB300 one pulled edge costs about four
+// pushed ones, so a level is pulled when the unreached vertices' edges times
+// this ratio are fewer than the frontier's.
+constexpr unsigned long long BC_PULL_RATIO = 4;
 static_assert(BC_WTILE == 256, "warp_tile_rows8 covers 256-position tiles");
 
 template <typename OffT>
 struct BcArgs {
     int64_t words;             // 32-vertex words of the bitmap
+    int64_t ne;                // edges of the graph
+    int mode;                  // 0 edge-count rule, 1 forward push / backward pull only, 2 the other way only
+    const uint32_t *nz;        // non-isolated bitmap
     const OffT *ro;
     const int32_t *col;
     uint32_t *code;            // 2-bit level codes, 16 vertices per word (3 = unreached)
@@ -69,7 +90,8 @@ struct BcArgs {
     int32_t src;
 };
 
-enum { BOP_FWD, BOP_FWD_BMP, BOP_FWD_FINAL, BOP_DEEPEST, BOP_BACK, BOP_BACK_FIX };
+enum { BOP_FWD, BOP_FWD_BMP, BOP_FWD_FINAL, BOP_FWD_PULL, BOP_DEEPEST, BOP_BACK, BOP_BACK_FIX,
+       BOP_BACK_PUSH, BOP_BACK_FIN };
 
 struct BcState {
     int d;                     // level being processed
@@ -79,6 +101,8 @@ struct BcState {
     int phase;                 // phases run so far
     uint32_t start, q, T;      // level d: first list index, vertices, edges
     uint32_t fq;               // fix-up phase: listed vertices
+    uint32_t ps, pq, pT;       // backward: level d + 1's list slice and edges
+    unsigned long long seenE;  // forward: edges of the levels up to d
 };
 
 template <typename OffT>
@@ -89,7 +113,10 @@ union BcWarpSmem {
         double val[BC_WTILE + 1];   // forward: sigma of the element; backward: its row's tile sum
         alignas(16) uint16_t rid[BC_WTILE];
     };
-    uint16_t list[32 * 32];         // finalize: compacted bits of a 32-word chunk
+    struct {
+        uint16_t list[32 * 32];     // finalize / pull: compacted bits of a 32-word chunk
+        uint32_t fb[32];            // pull: bits of the chunk's vertices that joined level d + 1
+    };
 };
 
 __device__ __forceinline__ uint32_t level_code(const uint32_t *code, int32_t v) {
@@ -107,8 +134,10 @@ __device__ __forceinline__ uint32_t spread16(uint32_t x) {
 }
 
 // Stages the level elements that start before e1 (from index i0) into shared
-// memory; returns their count.  Forward also stages sigma of each element.
-template <typename OffT, bool BACK>
+// memory; returns their count, with sigma or acc of each element if asked.
+enum { STAGE_SIGMA, STAGE_NONE, STAGE_ACC };
+
+template <typename OffT, int WHAT>
 __device__ __forceinline__ int stage_elements(const BcArgs<OffT> &a, const int32_t *Qv, const uint32_t *Qe,
                                               const OffT *Qr, int64_t q, int64_t i0, uint32_t e1,
                                               BcWarpSmem<OffT> &w) {
@@ -122,7 +151,8 @@ __device__ __forceinline__ int stage_elements(const BcArgs<OffT> &a, const int32
         if (n + (int)lane <= BC_WTILE + 1) w.qe[n + lane] = qe;
         if (in && n + (int)lane <= BC_WTILE) {
             w.rs[n + lane] = __ldcg(Qr + idx);
-            if (!BACK) w.val[n + lane] = __ldcg(a.sigma + __ldcg(Qv + idx));
+            if (WHAT == STAGE_SIGMA) w.val[n + lane] = __ldcg(a.sigma + __ldcg(Qv + idx));
+            if (WHAT == STAGE_ACC) w.val[n + lane] = __ldcg(a.acc + __ldcg(Qv + idx));
         }
         const int cnt = __popc(__ballot_sync(GRX_FULL_MASK, in));
         n += cnt;
@@ -178,7 +208,7 @@ __device__ void forward_level(const BcArgs<OffT> &a, const BcState &st, BcWarpSm
     for (uint64_t tile = tb0; tile < tb1; ++tile) {
         const uint64_t e0 = tile * BC_WTILE;
         const uint32_t e1 = (uint32_t)min(T, e0 + BC_WTILE);
-        const int n = stage_elements<OffT, false>(a, Qv, Qe, Qr, st.q, i0, e1, w);
+        const int n = stage_elements<OffT, STAGE_SIGMA>(a, Qv, Qe, Qr, st.q, i0, e1, w);
         const uint32_t next_start = w.qe[n];
         int row[BC_ITEMS];
         warp_tile_rows8(w.rid, w.qe, (uint32_t)e0, n, row);
@@ -312,7 +342,7 @@ __device__ void backward_level(const BcArgs<OffT> &a, const BcState &st, BcWarpS
     for (uint64_t tile = tb0; tile < tb1; ++tile) {
         const uint64_t e0 = tile * BC_WTILE;
         const uint32_t e1 = (uint32_t)min(T, e0 + BC_WTILE);
-        const int n = stage_elements<OffT, true>(a, Qv, Qe, Qr, st.q, i0, e1, w);
+        const int n = stage_elements<OffT, STAGE_NONE>(a, Qv, Qe, Qr, st.q, i0, e1, w);
         const uint32_t next_start = w.qe[n];
         int row[BC_ITEMS];
         warp_tile_rows8(w.rid, w.qe, (uint32_t)e0, n, row);
@@ -408,6 +438,177 @@ __device__ void backward_level(const BcArgs<OffT> &a, const BcState &st, BcWarpS
     }
 }
 
+// Even bits of x's 2-bit fields that equal 3 (unreached), packed into 16 bits.
+__device__ __forceinline__ uint32_t unreached16(uint32_t x) {
+    x = x & (x >> 1) & 0x55555555u;
+    x = (x | (x >> 1)) & 0x33333333u;
+    x = (x | (x >> 2)) & 0x0f0f0f0fu;
+    x = (x | (x >> 4)) & 0x00ff00ffu;
+    x = (x | (x >> 8)) & 0x0000ffffu;
+    return x;
+}
+
+// Forward pull of level d: the owner of each 32-word chunk sums, for every
+// unreached non-isolated vertex of the chunk, sigma over its neighbours at
+// depth d; a vertex with such a neighbour joins level d + 1 (sigma, code,
+// appended in vertex order).  Rows longer than 32 edges are summed by the
+// whole warp.
+template <typename OffT>
+__device__ void forward_pull(const BcArgs<OffT> &a, const BcState &st, BcWarpSmem<OffT> &w) {
+    const int d = st.d;
+    const uint32_t cd = (uint32_t)(d % 3);
+    const uint32_t cpat = (uint32_t)((d + 1) % 3) * 0x55555555u;
+    int32_t *Qv_out = a.Q + st.start + st.q;
+    uint32_t *Qe_out = a.E + st.start + st.q;
+    OffT *Qr_out = a.R + st.start + st.q;
+    unsigned long long *ctr = &a.ctl->qpack[(d + 1) & 3];
+    const unsigned int lane = threadIdx.x & 31;
+    const int64_t nsc = (a.words + 31) / 32;
+    const int64_t nwarps = (int64_t)gridDim.x * BC_WARPS;
+    for (int64_t sc = (int64_t)blockIdx.x * BC_WARPS + (threadIdx.x >> 5); sc < nsc; sc += nwarps) {
+        const int64_t wd = sc * 32 + lane;
+        uint32_t cand = 0u;
+        if (wd < a.words)
+            cand = (unreached16(__ldcg(a.code + 2 * wd)) | (unreached16(__ldcg(a.code + 2 * wd + 1)) << 16)) &
+                   __ldg(a.nz + wd);
+        w.fb[lane] = 0u;
+        const int n = warp_compact_bits(cand, w.list);
+        for (int base = 0; base < n; base += 32) {
+            const int i = base + (int)lane;
+            const int32_t v = i < n ? (int32_t)(sc * 1024 + w.list[i]) : -1;
+            OffT rb = 0;
+            uint32_t deg = 0;
+            if (v >= 0) {
+                rb = __ldg(a.ro + v);
+                deg = (uint32_t)(__ldg(a.ro + v + 1) - rb);
+            }
+            double s = 0.0;
+            const bool longrow = deg > 32u;
+            if (!longrow) {
+                for (uint32_t k = 0; k < deg; k += 4) {
+                    int32_t u[4];
+#pragma unroll
+                    for (int j = 0; j < 4; ++j) u[j] = k + j < deg ? __ldg(a.col + rb + (OffT)(k + j)) : -1;
+                    uint32_t cu[4];
+#pragma unroll
+                    for (int j = 0; j < 4; ++j) cu[j] = u[j] >= 0 ? level_code(a.code, u[j]) : 0xffu;
+#pragma unroll
+                    for (int j = 0; j < 4; ++j)
+                        if (cu[j] == cd) s += __ldcg(a.sigma + u[j]);
+                }
+            }
+            unsigned int lm = __ballot_sync(GRX_FULL_MASK, longrow);
+            while (lm) {
+                const int owner = __ffs(lm) - 1;
+                lm &= lm - 1;
+                const OffT lrb = __shfl_sync(GRX_FULL_MASK, rb, owner);
+                const uint32_t ldeg = __shfl_sync(GRX_FULL_MASK, deg, owner);
+                double ls = 0.0;
+                for (uint32_t k = lane; k < ldeg; k += 32) {
+                    const int32_t u = __ldg(a.col + lrb + (OffT)k);
+                    if (level_code(a.code, u) == cd) ls += __ldcg(a.sigma + u);
+                }
+#pragma unroll
+                for (int o = 16; o > 0; o >>= 1) ls += __shfl_xor_sync(GRX_FULL_MASK, ls, o);
+                if ((int)lane == owner) s = ls;
+            }
+            if (s > 0.0) {
+                a.sigma[v] = s;
+                atomicOr(&w.fb[(v >> 5) & 31], 1u << (v & 31));
+            }
+        }
+        __syncwarp();
+        const uint32_t bits = w.fb[lane];
+        if (bits) {
+#pragma unroll
+            for (int h = 0; h < 2; ++h) {
+                const uint32_t half = (bits >> (16 * h)) & 0xffffu;
+                if (half) {
+                    uint32_t m = spread16(half);
+                    m |= m << 1;
+                    uint32_t *cw = a.code + wd * 2 + h;
+                    *cw = (__ldcg(cw) & ~m) | (cpat & m);
+                }
+            }
+        }
+        const int m = warp_compact_bits(bits, w.list);
+        for (int base = 0; base < m; base += 32 * BC_RPL) {
+            int32_t v[BC_RPL];
+            uint32_t deg[BC_RPL];
+            OffT rb[BC_RPL];
+            uint32_t app = 0;
+#pragma unroll
+            for (int k = 0; k < BC_RPL; ++k) {
+                const int i = base + k * 32 + (int)lane;
+                v[k] = i < m ? (int32_t)(sc * 1024 + w.list[i]) : 0;
+                rb[k] = 0;
+                deg[k] = 0;
+                if (i < m) {
+                    rb[k] = __ldg(a.ro + v[k]);
+                    deg[k] = (uint32_t)(__ldg(a.ro + v[k] + 1) - rb[k]);
+                    if (deg[k]) app |= 1u << k;
+                }
+            }
+            warp_append_items<BC_RPL, OffT>(v, deg, rb, app, Qv_out, Qe_out, Qr_out, ctr);
+        }
+        __syncwarp();
+    }
+}
+
+// Backward push into level d: every vertex w of level d + 1 adds coef[w]
+// into acc[v] of its neighbours at depth d (float64 reductions).
+template <typename OffT>
+__device__ void backward_push(const BcArgs<OffT> &a, const BcState &st, BcWarpSmem<OffT> &w) {
+    const uint32_t cd = (uint32_t)(st.d % 3);
+    const unsigned int lane = threadIdx.x & 31;
+    const int32_t *Qv = a.Q + st.ps;
+    const uint32_t *Qe = a.E + st.ps;
+    const OffT *Qr = a.R + st.ps;
+    const uint64_t T = st.pT;
+    uint64_t tb0, tb1;
+    if (!warp_tiles(T, tb0, tb1)) return;
+    int64_t i0 = warp_upper_index_cg(Qe, st.pq, (uint32_t)(tb0 * BC_WTILE));
+    for (uint64_t tile = tb0; tile < tb1; ++tile) {
+        const uint64_t e0 = tile * BC_WTILE;
+        const uint32_t e1 = (uint32_t)min(T, e0 + BC_WTILE);
+        const int n = stage_elements<OffT, STAGE_ACC>(a, Qv, Qe, Qr, st.pq, i0, e1, w);
+        const uint32_t next_start = w.qe[n];
+        int row[BC_ITEMS];
+        warp_tile_rows8(w.rid, w.qe, (uint32_t)e0, n, row);
+        const uint32_t t0 = (uint32_t)e0 + lane * BC_ITEMS;
+        int32_t v[BC_ITEMS];
+        double x[BC_ITEMS];
+#pragma unroll
+        for (int k = 0; k < BC_ITEMS; ++k) {
+            const uint32_t e = t0 + k;
+            const int j = row[k];
+            const bool ok = e < e1;
+            const OffT idx = ok ? w.rs[j] + (OffT)(e - w.qe[j]) : (OffT)0;
+            v[k] = ok ? __ldg(a.col + idx) : -1;
+            x[k] = ok ? w.val[j] : 0.0;
+        }
+        __syncwarp();
+        uint32_t cv[BC_ITEMS];
+#pragma unroll
+        for (int k = 0; k < BC_ITEMS; ++k) cv[k] = v[k] >= 0 ? level_code(a.code, v[k]) : 0xffu;
+#pragma unroll
+        for (int k = 0; k < BC_ITEMS; ++k)
+            if (cv[k] == cd) atomicAdd(a.acc + v[k], x[k]);              // result unused: reduction
+        i0 = (next_start == e1) ? i0 + n : i0 + n - 1;
+        __syncwarp();
+    }
+}
+
+// After a backward push: every vertex of level d finishes from acc.
+template <typename OffT>
+__device__ void backward_fin(const BcArgs<OffT> &a, const BcState &st) {
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < (int64_t)st.q;
+         i += (int64_t)gridDim.x * blockDim.x) {
+        const int32_t v = __ldcg(a.Q + st.start + i);
+        finish_vertex(a, v, __ldcg(a.acc + v));
+    }
+}
+
 // After a backward level: the vertices whose rows crossed tiles.
 template <typename OffT>
 __device__ void backward_fix(const BcArgs<OffT> &a, const BcState &st) {
@@ -428,9 +629,28 @@ __device__ void deepest_level(const BcArgs<OffT> &a, const BcState &st) {
     }
 }
 
+// Kind of forward level d with T frontier edges; seenE = edges of the levels
+// up to d.  Pull when the still-unreached vertices have fewer edges.
 template <typename OffT>
-__device__ __forceinline__ int forward_op(const BcArgs<OffT> &a, uint32_t T) {
+__device__ __forceinline__ int forward_op(const BcArgs<OffT> &a, int d, uint32_t T, unsigned long long seenE) {
+    const unsigned long long left = (unsigned long long)a.ne > seenE ? (unsigned long long)a.ne - seenE : 0ull;
+    if (d > 0 && (a.mode == 2 || (a.mode == 0 && left * BC_PULL_RATIO < (unsigned long long)T)))
+        return BOP_FWD_PULL;
     return T >= a.bmp_min_T ? BOP_FWD_BMP : BOP_FWD;
+}
+
+// Backward level d (>= 1) after level d + 1 = (start, q, T) of st: its state.
+template <typename OffT>
+__device__ __forceinline__ BcState backward_state(const BcArgs<OffT> &a, const BcState &st, BcState ns) {
+    ns.d = st.d - 1;
+    ns.ps = st.start;
+    ns.pq = st.q;
+    ns.pT = st.T;
+    ns.start = ld_relaxed_u32(a.lstart + ns.d);
+    ns.q = st.start - ns.start;
+    ns.T = ld_relaxed_u32(a.ledges + ns.d);
+    ns.op = (a.mode == 2 || (a.mode == 0 && ns.pT < ns.T)) ? BOP_BACK_PUSH : BOP_BACK;
+    return ns;
 }
 
 template <typename OffT>
@@ -441,7 +661,7 @@ __device__ BcState bc_next(const BcArgs<OffT> &a, const BcState &st) {
         ns.op = BOP_FWD_FINAL;
         return ns;
     }
-    if (st.op == BOP_FWD || st.op == BOP_FWD_FINAL) {           // end of forward level d
+    if (st.op == BOP_FWD || st.op == BOP_FWD_FINAL || st.op == BOP_FWD_PULL) {   // end of forward level d
         const unsigned long long pk = ld_relaxed_u64(&a.ctl->qpack[(st.d + 1) & 3]);
         const uint32_t q = (uint32_t)(pk >> 32);
         if (q > 0) {
@@ -449,7 +669,8 @@ __device__ BcState bc_next(const BcArgs<OffT> &a, const BcState &st) {
             ns.start = st.start + st.q;
             ns.q = q;
             ns.T = (uint32_t)pk;
-            ns.op = forward_op(a, ns.T);
+            ns.seenE = st.seenE + ns.T;
+            ns.op = forward_op(a, ns.d, ns.T, ns.seenE);
         } else {
             ns.levels = st.d + 1;
             ns.op = BOP_DEEPEST;                                // level d is the deepest
@@ -465,20 +686,19 @@ __device__ BcState bc_next(const BcArgs<OffT> &a, const BcState &st) {
             return ns;
         }
     }
+    if (st.op == BOP_BACK_PUSH) {
+        ns.op = BOP_BACK_FIN;
+        return ns;
+    }
     if (st.d == 1) {                                            // level 0 is the source
         ns.done = 1;
         return ns;
     }
-    ns.op = BOP_BACK;
-    ns.d = st.d - 1;
-    ns.start = ld_relaxed_u32(a.lstart + ns.d);
-    ns.q = st.start - ns.start;
-    ns.T = ld_relaxed_u32(a.ledges + ns.d);
-    return ns;
+    return backward_state(a, st, ns);
 }
 
 template <typename OffT>
-__global__ void __launch_bounds__(BC_BLOCK) k_bc_persistent(BcArgs<OffT> a) {
+__global__ void __launch_bounds__(BC_BLOCK, GRX_BC_MIN_BLOCKS) k_bc_persistent(BcArgs<OffT> a) {
     __shared__ BcState s_st;
     __shared__ BcWarpSmem<OffT> wsm[BC_WARPS];
     BcWarpSmem<OffT> &w = wsm[threadIdx.x >> 5];
@@ -489,7 +709,8 @@ __global__ void __launch_bounds__(BC_BLOCK) k_bc_persistent(BcArgs<OffT> a) {
         const uint32_t deg = (uint32_t)(a.ro[a.src + 1] - a.ro[a.src]);
         s.q = 1;
         s.T = deg;
-        s.op = forward_op(a, deg);
+        s.seenE = deg;
+        s.op = forward_op(a, 0, deg, s.seenE);
         s.done = deg == 0;
         s.levels = 1;
         s_st = s;
@@ -499,19 +720,22 @@ __global__ void __launch_bounds__(BC_BLOCK) k_bc_persistent(BcArgs<OffT> a) {
         const BcState st = s_st;
         if (st.done) break;
         if (blockIdx.x == 0 && threadIdx.x == 0) {
-            if (st.op == BOP_FWD || st.op == BOP_FWD_BMP) {
+            if (st.op == BOP_FWD || st.op == BOP_FWD_BMP || st.op == BOP_FWD_PULL) {
                 a.ctl->qpack[(st.d + 2) & 3] = 0ull;
                 a.lstart[st.d] = st.start;
                 a.ledges[st.d] = st.T;
             }
-            // the fix-up counter of level d - 1 was last read two barriers ago
-            if (st.op == BOP_BACK) a.ctl->bcfix[(st.d + 2) % 3] = 0u;
+            // the fix-up counter of level d - 1 was last read at least two barriers ago
+            if (st.op == BOP_BACK || st.op == BOP_BACK_PUSH) a.ctl->bcfix[(st.d + 2) % 3] = 0u;
             if (a.stats && st.phase < GRX_MAX_LEVELS_STATS) {
                 // phases in order: forward levels (dir 0), then backward levels (dir 1)
                 a.stats->level_t0[st.phase] = grx_globaltimer();
                 a.stats->dir[st.phase] = st.op >= BOP_DEEPEST;
                 a.stats->frontier[st.phase] = st.op == BOP_BACK_FIX ? st.fq : st.q;
-                a.stats->edges_examined[st.phase] = (st.op == BOP_FWD_FINAL || st.op == BOP_BACK_FIX) ? 0 : st.T;
+                a.stats->edges_examined[st.phase] =
+                    st.op == BOP_BACK_PUSH ? st.pT
+                    : (st.op == BOP_FWD_FINAL || st.op == BOP_BACK_FIX || st.op == BOP_BACK_FIN) ? 0 : st.T;
+                a.stats->vertices_scanned[st.phase] = st.op;    // the phase's kind
                 a.stats->levels = st.phase + 1;
             }
         }
@@ -519,6 +743,9 @@ __global__ void __launch_bounds__(BC_BLOCK) k_bc_persistent(BcArgs<OffT> a) {
             case BOP_FWD: forward_level<OffT, false>(a, st, w); break;
             case BOP_FWD_BMP: forward_level<OffT, true>(a, st, w); break;
             case BOP_FWD_FINAL: forward_final<OffT>(a, st, w.list); break;
+            case BOP_FWD_PULL: forward_pull<OffT>(a, st, w); break;
+            case BOP_BACK_PUSH: backward_push<OffT>(a, st, w); break;
+            case BOP_BACK_FIN: backward_fin<OffT>(a, st); break;
             case BOP_DEEPEST: deepest_level<OffT>(a, st); break;
             case BOP_BACK_FIX: {
                 BcState fs = st;
@@ -555,6 +782,9 @@ grx_status launch_typed(grx_graph *g, const int32_t *srcs, int n, double *bc_out
                         cudaStream_t s) {
     BcArgs<OffT> a;
     a.words = g->words;
+    a.ne = g->ne;
+    a.mode = o->direction;
+    a.nz = g->nz_bits;
     a.ro = (const OffT *)g->ro;
     a.col = g->col;
     a.code = g->bc_code;

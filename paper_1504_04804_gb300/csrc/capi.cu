@@ -450,6 +450,8 @@ extern "C" grx_status bc(grx_graph *g, const int32_t *srcs_host, int n, double *
     if (!bc_out) return grx_fail(GRX_EINVAL, "bc: bc_out is NULL");
     grx_opts o;
     grx_resolve_opts(opts, &o);
+    if (o.direction < GRX_DIR_AUTO || o.direction > GRX_DIR_PULL)
+        return grx_fail(GRX_EINVAL, "bc: bad direction %d", o.direction);
     g->last_stream = stream;
     cudaStream_t s = (cudaStream_t)stream;
     if ((st = grx_ensure_workspace(g, s))) return st;

@@ -57,7 +57,8 @@ def test_sssp_cc_pagerank_at_scale_22(big):
 
 def test_bc_at_scale_22(big):
     grx, g, (ro, col, _), srcs = big
-    got, sig = grx.bc(g, [srcs[0]], want_sigma=True)
     want, wsig = oracle.bc(ro, col, [srcs[0]], want_sigma=True)
-    np.testing.assert_allclose(got.cpu().numpy(), want, rtol=1e-9, atol=0)
-    np.testing.assert_allclose(sig.cpu().numpy(), wsig, rtol=1e-12, atol=0)
+    for mode in (0, 1, 2):
+        got, sig = grx.bc(g, [srcs[0]], want_sigma=True, opts=grx.opts(direction=mode))
+        np.testing.assert_allclose(got.cpu().numpy(), want, rtol=1e-9, atol=0, err_msg=str(mode))
+        np.testing.assert_allclose(sig.cpu().numpy(), wsig, rtol=1e-12, atol=0, err_msg=str(mode))

@@ -434,9 +434,13 @@ BC_TOL = 1e-9
 
 @pytest.mark.parametrize("name", list(GRAPHS))
 @pytest.mark.parametrize("pb", list(PUSH_BITMAP))
-def test_bc_single_sources_match_oracle(grx, loaded, name, pb):
+@pytest.mark.parametrize("mode", list(MODES))
+def test_bc_single_sources_match_oracle(grx, loaded, name, pb, mode):
+    """mode: auto = direction per level by edge counts; push = forward push
+    and backward pull only; pull = forward pull (after the source level) and
+    backward push only."""
     g, dg = GRAPHS[name], loaded[name]
-    o = grx.opts(push_bitmap=PUSH_BITMAP[pb])
+    o = grx.opts(push_bitmap=PUSH_BITMAP[pb], direction=MODES[mode])
     for s in _sources(g, 3, seed=4) + [0, g.nv - 1]:
         got, sig = grx.bc(dg, [s], want_sigma=True, opts=o)
         want, wsig = oracle.bc(g.row_offsets, g.col_indices, [s], want_sigma=True)
@@ -449,8 +453,10 @@ def test_bc_sums_over_sources_match_oracle(grx, loaded, name):
     g, dg = GRAPHS[name], loaded[name]
     srcs = _sources(g, 6, seed=5)
     srcs += srcs[:2]                                     # duplicates count twice
-    got = grx.bc(dg, srcs).cpu().numpy()
-    np.testing.assert_allclose(got, oracle.bc(g.row_offsets, g.col_indices, srcs), rtol=BC_TOL, atol=0)
+    want = oracle.bc(g.row_offsets, g.col_indices, srcs)
+    for mode in MODES.values():
+        got = grx.bc(dg, srcs, opts=grx.opts(direction=mode)).cpu().numpy()
+        np.testing.assert_allclose(got, want, rtol=BC_TOL, atol=0, err_msg=str(mode))
 
 
 def test_bc_every_source_of_every_5_vertex_graph(grx):
@@ -466,8 +472,10 @@ def test_bc_every_source_of_every_5_vertex_graph(grx):
         u = inputs.csr_from_edges(n * len(masks), edges)
         du = grx.load(u, validate=True)
         srcs = np.arange(u.nv)
-        np.testing.assert_allclose(grx.bc(du, srcs).cpu().numpy(),
-                                   oracle.bc(u.row_offsets, u.col_indices, srcs), rtol=BC_TOL, atol=0)
+        want = oracle.bc(u.row_offsets, u.col_indices, srcs)
+        for mode in MODES.values():
+            np.testing.assert_allclose(grx.bc(du, srcs, opts=grx.opts(direction=mode)).cpu().numpy(),
+                                       want, rtol=BC_TOL, atol=0, err_msg=str(mode))
 
 
 def test_bc_int64_offsets_and_edge_cases(grx):
