@@ -102,16 +102,18 @@ def cc_bytes(nv: int, hooked: int, off_bytes: int) -> int:
     return hooked * 12 + 3 * nv * (off_bytes + 4) + 3 * nv * 8
 
 
-def bc_bytes(nv: int, v_r: int, e_r: int, e_dag: int, off_bytes: int) -> int:
+def bc_bytes(nv: int, v_r: int, e_read: int, e_dag: int, off_bytes: int) -> int:
     """Betweenness centrality, one source: sigma and acc initialised (16
     bytes per vertex), 2-bit level codes and the next-level bitmap (3 bits);
     per reached vertex, forward row offsets 2o, level list write and read
     2(8+o), sigma 8 and the code update 4, backward list (8+o), sigma 8,
-    coefficient 8 and the bc update 16; per reached edge, in both passes,
-    column and level-code word (8 + 8); per shortest-path DAG edge, the
-    sigma reduction 16 and the coefficient gather 8."""
+    coefficient 8 and the bc update 16; per edge a phase reads (the kernel's
+    per-phase counts: pull and push levels skip the rest), column and
+    level-code word (4 + 4); per shortest-path DAG edge, the parent's sigma
+    in the forward sweep and the successor's coefficient in the backward
+    one (8 + 8)."""
     o = off_bytes
-    return nv * 16 + (3 * nv) // 8 + v_r * (2 * o + 2 * (8 + o) + 12 + (8 + o) + 32) + e_r * 16 + e_dag * 24
+    return nv * 16 + (3 * nv) // 8 + v_r * (2 * o + 2 * (8 + o) + 12 + (8 + o) + 32) + e_read * 8 + e_dag * 16
 
 
 def dag_edges(ro_h, col_dev, depth_dev) -> int:
@@ -580,11 +582,12 @@ def grid_workload(args):
     def sssp_rounds(delta):
         grx.sssp(g, srcs[0], opts=grx.opts(collect_stats=1, sssp_delta=delta))
         st = grx.last_stats(g)
-        return st["levels"], int(sum(st["edges_examined"]))
+        return st["levels"], int(sum(st["edges_examined"])), sssp_bytes(st, 4)
     ss = sssp_times(grx.opts())
-    rounds, relaxed = sssp_rounds(0)
+    rounds, relaxed, sb = sssp_rounds(0)
     nf = sssp_times(grx.opts(sssp_delta=tuned["sssp_delta"]))
-    nf_rounds, nf_relaxed = sssp_rounds(tuned["sssp_delta"])
+    nf_rounds, nf_relaxed, nfb = sssp_rounds(tuned["sssp_delta"])
+    peak, _ = _peaks()
     grx.graph_status(g)
     best = min(t.values())
     line = {"metric": METRIC, "value": edges / (t["persistent"] / 1e3) / 1e9, "unit": "GTEPS",
@@ -597,9 +600,11 @@ def grid_workload(args):
             "bfs_levels_per_s": {k: levels / (v / 1e3) for k, v in t.items()},
             "sssp_ms": ss, "sssp_rounds": rounds, "sssp_edges_relaxed": relaxed,
             "sssp_gteps": edges / (statistics.median(ss) / 1e3) / 1e9,
+            "sssp_roofline_frac": sb / (ss[0] / 1e3) / 1e9 / peak,
             "sssp_near_far": {"delta": tuned["sssp_delta"], "tuning_s": tuned["seconds"], "ms": nf,
                               "rounds": nf_rounds, "edges_relaxed": nf_relaxed,
-                              "gteps": edges / (statistics.median(nf) / 1e3) / 1e9}}
+                              "gteps": edges / (statistics.median(nf) / 1e3) / 1e9,
+                              "roofline_frac": nfb / (nf[0] / 1e3) / 1e9 / peak}}
     print(json.dumps(line), flush=True)
     return 0
 
@@ -721,19 +726,23 @@ def other_primitives(grx, g, srcs, nv, ne, off_bytes, deg_h, flush, stream, peak
                        "roofline_frac": pb / (statistics.median(ts) / 1e3) / 1e9 / peak}
     # betweenness centrality: one source per call, 4 sources
     bco = torch.empty(nv, dtype=torch.float64, device=flush.device)
-    bbytes, bedges, dags = [], [], []
+    bbytes, bedges, dags, reads = [], [], [], []
     for s in srcs[:4]:
         dep = grx.bfs(g, s)
         reached = dep.cpu().numpy() >= 0
         e_r = int(deg_h[reached].sum())
         v_r = int(np.count_nonzero(reached & (deg_h > 0)))
         e_dag = dag_edges(ro_h, col_dev, dep) if col_dev is not None else e_r // 2
+        grx.bc(g, [s], bc_out=bco, opts=grx.opts(collect_stats=1))
+        e_read = int(sum(grx.last_stats(g)["edges_examined"]))
         dags.append(e_dag)
+        reads.append(e_read)
         bedges.append(e_r)
-        bbytes.append(bc_bytes(nv, v_r, e_r, e_dag, off_bytes))
+        bbytes.append(bc_bytes(nv, v_r, e_read, e_dag, off_bytes))
     ts = timed(lambda i: grx.bc(g, [srcs[i % 4]], bc_out=bco), 4)
     grx.graph_status(g)
     out["bc"] = {"ms": ts, "gteps": sum(bedges) / (sum(ts) / 1e3) / 1e9, "dag_edges": dags,
+                 "edges_read": reads,
                  "roofline_frac": sum(bbytes) / (sum(ts) / 1e3) / 1e9 / peak,
                  "note": "one source per call; GTEPS counts each reached edge once"}
     return out

@@ -199,7 +199,9 @@ grx_status sssp_multi(grx_graph *g, const int32_t *srcs_host, int n, uint32_t *d
  * GRX_DIR_PULL the other way round (after the source level).  Uses about
  * 16 bytes of workspace per vertex.  With opts->collect_stats, grx_last_stats describes the last
  * source's phases: forward levels (dir 0) then backward levels (dir 1),
- * frontier = the level's vertices, edges_examined = their edges.
+ * frontier = the level's vertices, edges_examined = the edges the phase
+ * reads (a forward pull: the unreached vertices' rows; a backward push: the
+ * rows of the level below), vertices_scanned = the phase's kind.
  * Bad source or NULL output -> GRX_EINVAL. */
 grx_status bc(grx_graph *g, const int32_t *srcs_host, int n, double *bc_out, double *sigma_out,
               const grx_opts *opts, void *stream);

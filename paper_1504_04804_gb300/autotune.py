@@ -122,13 +122,13 @@ def tune_bfs(g, row_offsets, n_sources: int = 8, seed: int = 2, reps: int = 2,
     return dict(res, cached=False)
 
 
-DELTA_FACTORS = (0, 4, 16, 64, 256)
+DELTA_FACTORS = (0, 4, 16, 64, 256, 1024, 4096)
 
 
 def tune_sssp_delta(g, row_offsets, weights, n_sources: int = 2, seed: int = 3,
                     cache: str | None = DEFAULT_CACHE, force: bool = False) -> dict:
     """Near-far band width for SSSP on a loaded weighted graph: 0 (plain
-    label-correcting rounds) or the mean edge weight times 4, 16, 64 or 256
+    label-correcting rounds) or the mean edge weight times 4 ... 4096
     (Davidson et al. scale the band with the weights), whichever gives the
     smallest total kernel time over the tuning sources.
     Returns {"sssp_delta", "ms", "tried", "seconds", "fingerprint", "cached"}."""

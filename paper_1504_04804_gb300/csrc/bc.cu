@@ -732,8 +732,11 @@ __global__ void __launch_bounds__(BC_BLOCK, GRX_BC_MIN_BLOCKS) k_bc_persistent(B
                 a.stats->level_t0[st.phase] = grx_globaltimer();
                 a.stats->dir[st.phase] = st.op >= BOP_DEEPEST;
                 a.stats->frontier[st.phase] = st.op == BOP_BACK_FIX ? st.fq : st.q;
+                // edges the phase reads: a forward pull reads the unreached vertices' rows,
+                // a backward push the rows of level d + 1
                 a.stats->edges_examined[st.phase] =
                     st.op == BOP_BACK_PUSH ? st.pT
+                    : st.op == BOP_FWD_PULL ? ((unsigned long long)a.ne > st.seenE ? a.ne - st.seenE : 0)
                     : (st.op == BOP_FWD_FINAL || st.op == BOP_BACK_FIX || st.op == BOP_BACK_FIN) ? 0 : st.T;
                 a.stats->vertices_scanned[st.phase] = st.op;    // the phase's kind
                 a.stats->levels = st.phase + 1;
