@@ -741,6 +741,14 @@ def other_primitives(grx, g, srcs, nv, ne, off_bytes, deg_h, flush, stream, peak
         bbytes.append(bc_bytes(nv, v_r, e_read, e_dag, off_bytes))
     ts = timed(lambda i: grx.bc(g, [srcs[i % 4]], bc_out=bco), 4)
     grx.graph_status(g)
+    # batched BC: the 64 multi-source lanes in one sweep (float64 rows of 64 lanes per vertex)
+    if nv * 1100 < torch.cuda.mem_get_info()[0] // 2:
+        bm = torch.empty(nv, dtype=torch.float64, device=flush.device)
+        tsm = timed(lambda i: grx.bc_multi(g, lanes, bc_out=bm), 2)
+        grx.graph_status(g)
+        out["bc_multi_64"] = {"ms": tsm, "per_source_ms": statistics.median(tsm) / 64,
+                              "one_by_one_per_source_ms": statistics.median(ts) if ts else None,
+                              "gteps": ms_edges / (statistics.median(tsm) / 1e3) / 1e9}
     out["bc"] = {"ms": ts, "gteps": sum(bedges) / (sum(ts) / 1e3) / 1e9, "dag_edges": dags,
                  "edges_read": reads,
                  "roofline_frac": sum(bbytes) / (sum(ts) / 1e3) / 1e9 / peak,

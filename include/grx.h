@@ -206,6 +206,18 @@ grx_status sssp_multi(grx_graph *g, const int32_t *srcs_host, int n, uint32_t *d
 grx_status bc(grx_graph *g, const int32_t *srcs_host, int n, double *bc_out, double *sigma_out,
               const grx_opts *opts, void *stream);
 
+/* bc_multi -- the same sum as bc() for up to 64 sources (n in 1..64,
+ * duplicates allowed), computed in one forward and one backward sweep shared
+ * by all sources: per vertex 64-bit lane masks and a 64-lane float64 row of
+ * path counts and of successor sums (every lane is one source's Brandes
+ * traversal).  bc_out: device float64[nv], overwritten.  Needs about
+ * 1,040 + 8 * GRX_BCM_MAX_LEVELS bytes of workspace per vertex (allocated on
+ * first use).  Graphs deeper than GRX_BCM_MAX_LEVELS - 1 levels set
+ * GRX_ERANGE (use bc() there).  The graph must be symmetric. */
+#define GRX_BCM_MAX_LEVELS 16
+grx_status bc_multi(grx_graph *g, const int32_t *srcs_host, int n, double *bc_out, const grx_opts *opts,
+                    void *stream);
+
 /* cc -- Table 1 CC (Soman et al.'s hooking + pointer jumping).  label_out:
  * device int32[nv], the minimum vertex id of the vertex's component. */
 grx_status cc(grx_graph *g, int32_t *label_out, void *stream);

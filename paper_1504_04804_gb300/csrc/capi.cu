@@ -498,6 +498,31 @@ static grx_status check_sources(grx_graph *g, const int32_t *srcs, int n, const 
     return GRX_OK;
 }
 
+extern "C" grx_status bc_multi(grx_graph *g, const int32_t *srcs_host, int n, double *bc_out,
+                               const grx_opts *opts, void *stream) {
+    grx_status st = check_graph(g, "bc_multi");
+    if (st) return st;
+    if ((st = check_sources(g, srcs_host, n, "bc_multi"))) return st;
+    if (!bc_out) return grx_fail(GRX_EINVAL, "bc_multi: bc_out is NULL");
+    grx_opts o;
+    grx_resolve_opts(opts, &o);
+    g->last_stream = stream;
+    cudaStream_t s = (cudaStream_t)stream;
+    if ((st = grx_ensure_workspace(g, s))) return st;
+    if (!g->bcm_sig) {
+        const size_t nv = (size_t)g->nv;
+        g->bcm_seen = (unsigned long long *)grx_alloc(g, nv * 8, s);
+        g->bcm_next = (unsigned long long *)grx_alloc(g, nv * 8, s);
+        g->bcm_hist = (unsigned long long *)grx_alloc(g, nv * 8 * GRX_BCM_MAX_LEVELS, s);
+        g->bcm_sig = (double *)grx_alloc(g, nv * 64 * 8, s);
+        g->bcm_acc = (double *)grx_alloc(g, nv * 64 * 8, s);
+        g->bcm_srcs = (int32_t *)grx_alloc(g, 64 * 4, s);
+        if (!g->bcm_seen || !g->bcm_next || !g->bcm_hist || !g->bcm_sig || !g->bcm_acc || !g->bcm_srcs)
+            return grx_fail(GRX_ENOMEM, "bc_multi: workspace allocation failed (nv=%d)", g->nv);
+    }
+    return grx_bcm_launch(g, srcs_host, n, bc_out, &o, s);
+}
+
 extern "C" grx_status bfs_multi(grx_graph *g, const int32_t *srcs_host, int n, int32_t *depth_out,
                                 const grx_opts *opts, void *stream) {
     grx_status st = check_graph(g, "bfs_multi");

@@ -127,11 +127,16 @@ struct grx_graph {
     // betweenness centrality (allocated on first use)
     double *bc_sigma, *bc_acc;       // [nv] each: path counts; successor sums / coefficients
     uint32_t *bc_code;               // [2 * words]: 2-bit level codes
+    // batched betweenness centrality (allocated on first use)
+    unsigned long long *bcm_seen, *bcm_next;   // [nv] lane masks
+    unsigned long long *bcm_hist;    // [GRX_BCM_MAX_LEVELS][nv] lanes at each depth
+    double *bcm_sig, *bcm_acc;       // [nv][64]
+    int32_t *bcm_srcs;               // [64] device copy of the sources
     // CUDA-graph level loop of bfs (GRX_LOOP_GRAPH), per parent flag
     cudaGraphExec_t bfs_gexec[2];
     void *bfs_gargs;                 // device copy of the call's arguments
     // bookkeeping for frees
-    struct Alloc { void *p; size_t n; } allocs[64];
+    struct Alloc { void *p; size_t n; } allocs[96];
     int nallocs;
 };
 
@@ -174,6 +179,8 @@ grx_status grx_sssp_launch(grx_graph *g, int32_t src, uint32_t *dist, const grx_
 grx_status grx_cc_launch(grx_graph *g, int32_t *label, const grx_opts *o, cudaStream_t s);
 grx_status grx_bc_launch(grx_graph *g, const int32_t *srcs, int n, double *bc_out, double *sigma_out,
                          const grx_opts *o, cudaStream_t s);
+grx_status grx_bcm_launch(grx_graph *g, const int32_t *srcs, int n, double *bc_out, const grx_opts *o,
+                          cudaStream_t s);
 grx_status grx_pr_launch(grx_graph *g, float damping, int iters, float *rank,
                          cudaStream_t s);
 

@@ -77,6 +77,7 @@ SIGNATURES = [
     ("sssp", _I, [_P, ctypes.c_int32, _P, _P, _P]),
     ("cc", _I, [_P, _P, _P]),
     ("bc", _I, [_P, _P, _I, _P, _P, _P, _P]),
+    ("bc_multi", _I, [_P, _P, _I, _P, _P, _P]),
     ("pagerank", _I, [_P, ctypes.c_float, _I, _P, _P]),
     ("grx_pagerank_block", _I, [_P, _I]),
     ("grx_last_stats", _I, [_P, _P, _P]),
@@ -330,6 +331,16 @@ def bc(g: Graph, srcs, bc_out=None, sigma_out=None, opts: grx_opts | None = None
                     sig.data_ptr() if sig is not None else None,
                     ctypes.byref(opts) if opts is not None else None, _stream_ptr(stream)), "bc")
     return (out, sig) if sig is not None else out
+
+
+def bc_multi(g: Graph, srcs, bc_out=None, opts: grx_opts | None = None, stream=None):
+    """The sum over up to 64 sources of Brandes' dependencies, computed in
+    one shared sweep; float64 tensor [nv]."""
+    arr, p, n = _srcs_arg(srcs)
+    out = _out(bc_out, g.nv, torch.float64, g.device)
+    _check(lib().bc_multi(g.handle, p, n, out.data_ptr(),
+                          ctypes.byref(opts) if opts is not None else None, _stream_ptr(stream)), "bc_multi")
+    return out
 
 
 def cc(g: Graph, label_out=None, stream=None):

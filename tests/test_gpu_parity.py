@@ -496,3 +496,48 @@ def test_bc_int64_offsets_and_edge_cases(grx):
         grx.bc(dd, [40])
     with pytest.raises(RuntimeError):
         grx.bc(dd, [])
+
+
+# ---- batched BC: up to 64 sources in one sweep, same sums as bc()
+
+@pytest.mark.parametrize("name", ["rmat10", "rmat13", "rmat14_ef4", "star", "disconnected"])
+def test_bc_multi_matches_oracle(grx, loaded, name):
+    g, dg = GRAPHS[name], loaded[name]
+    for n in (1, 7, 64):
+        srcs = _sources(g, n, seed=9)
+        srcs += srcs[:2] if len(srcs) < 64 else []       # duplicates allowed
+        srcs = srcs[:64]
+        got = grx.bc_multi(dg, srcs).cpu().numpy()
+        grx.graph_status(dg)
+        np.testing.assert_allclose(got, oracle.bc(g.row_offsets, g.col_indices, srcs), rtol=BC_TOL, atol=0,
+                                   err_msg=f"{name} n={len(srcs)}")
+
+
+def test_bc_multi_every_source_of_every_5_vertex_graph(grx):
+    n = 5
+    pairs = list(itertools.combinations(range(n), 2))
+    edges = []
+    for gi in range(1 << len(pairs)):
+        edges += [(gi * n + a, gi * n + b) for pi, (a, b) in enumerate(pairs) if gi >> pi & 1]
+    u = inputs.csr_from_edges(n * (1 << len(pairs)), edges)
+    du = grx.load(u, validate=True, offsets64=True)
+    total = np.zeros(u.nv)
+    out = torch.empty(u.nv, dtype=torch.float64, device="cuda")
+    for b in range(0, u.nv, 64):
+        total += grx.bc_multi(du, np.arange(b, min(u.nv, b + 64)), bc_out=out).cpu().numpy()
+    grx.graph_status(du)
+    np.testing.assert_allclose(total, oracle.bc(u.row_offsets, u.col_indices, np.arange(u.nv)),
+                               rtol=BC_TOL, atol=0)
+
+
+def test_bc_multi_too_deep_reports_range_and_recovers(grx, loaded):
+    dg = loaded["path"]                                  # 3,000 levels
+    grx.bc_multi(dg, [0, 5])
+    with pytest.raises(RuntimeError):
+        grx.graph_status(dg)
+    g = GRAPHS["rmat10"]
+    srcs = _sources(g, 4, seed=3)
+    np.testing.assert_allclose(grx.bc_multi(loaded["rmat10"], srcs).cpu().numpy(),
+                               oracle.bc(g.row_offsets, g.col_indices, srcs), rtol=BC_TOL, atol=0)
+    with pytest.raises(RuntimeError):
+        grx.bc_multi(dg, list(range(65)))
