@@ -116,6 +116,20 @@ def bc_bytes(nv: int, v_r: int, e_read: int, e_dag: int, off_bytes: int) -> int:
     return nv * 16 + (3 * nv) // 8 + v_r * (2 * o + 2 * (8 + o) + 12 + (8 + o) + 32) + e_read * 8 + e_dag * 16
 
 
+def bcm_bytes(nv: int, st: dict, pairs: int) -> int:
+    """Batched BC (64 lanes): zeroed 64-lane rows of path counts and sums
+    (1,024 bytes per vertex), lane masks (seen, next, depth-0 level: 24),
+    each further level's mask array zeroed (8 per vertex); per edge a phase
+    reads, column and the other end's lane mask (4 + 8); per shortest-path
+    (edge, lane), the source row value and the reduction into the target row
+    (8 + 16) in each sweep; per reached (vertex, lane), finishing reads the
+    sum and the path count and writes the coefficient (24)."""
+    levels = sum(1 for i in range(st["levels"]) if st["dir"][i] == 0) // 2
+    lane_edges = sum(st["vertices_scanned"][:st["levels"]])
+    return nv * (1024 + 24) + levels * nv * 8 + sum(st["edges_examined"][:st["levels"]]) * 12 \
+        + lane_edges * 24 + pairs * 24
+
+
 def dag_edges(ro_h, col_dev, depth_dev) -> int:
     """Edges (u, w) with depth[w] = depth[u] + 1, counted on the device in
     chunks of about 2^27 edges."""
@@ -703,7 +717,10 @@ def other_primitives(grx, g, srcs, nv, ne, off_bytes, deg_h, flush, stream, peak
     lanes =[int(s) for s in inputs.pick_sources(np.concatenate([[0], np.cumsum(deg_h)]), 64, seed=11)]
     dm = torch.empty(64 * nv, dtype=torch.int32, device=flush.device)
     grx.bfs_multi(g, lanes, depth_out=dm)
-    ms_edges = int(sum(int(deg_h[row >= 0].sum()) for row in dm.view(64, nv).cpu().numpy()))
+    dmh = dm.view(64, nv).cpu().numpy()
+    ms_edges = int(sum(int(deg_h[row >= 0].sum()) for row in dmh))
+    ms_pairs = int((dmh >= 0).sum())
+    del dmh
     ts = timed(lambda i: grx.bfs_multi(g, lanes, depth_out=dm), 3)
     grx.bfs_multi(g, lanes, depth_out=dm, opts=grx.opts(collect_stats=1))
     mb = msbfs_bytes(grx.last_stats(g), nv, off_bytes, 64)
@@ -746,9 +763,12 @@ def other_primitives(grx, g, srcs, nv, ne, off_bytes, deg_h, flush, stream, peak
         bm = torch.empty(nv, dtype=torch.float64, device=flush.device)
         tsm = timed(lambda i: grx.bc_multi(g, lanes, bc_out=bm), 2)
         grx.graph_status(g)
+        grx.bc_multi(g, lanes, bc_out=bm, opts=grx.opts(collect_stats=1))
+        mbytes = bcm_bytes(nv, grx.last_stats(g), ms_pairs)
         out["bc_multi_64"] = {"ms": tsm, "per_source_ms": statistics.median(tsm) / 64,
                               "one_by_one_per_source_ms": statistics.median(ts) if ts else None,
-                              "gteps": ms_edges / (statistics.median(tsm) / 1e3) / 1e9}
+                              "gteps": ms_edges / (statistics.median(tsm) / 1e3) / 1e9,
+                              "roofline_frac": mbytes / (statistics.median(tsm) / 1e3) / 1e9 / peak}
     out["bc"] = {"ms": ts, "gteps": sum(bedges) / (sum(ts) / 1e3) / 1e9, "dag_edges": dags,
                  "edges_read": reads,
                  "roofline_frac": sum(bbytes) / (sum(ts) / 1e3) / 1e9 / peak,

@@ -541,3 +541,21 @@ def test_bc_multi_too_deep_reports_range_and_recovers(grx, loaded):
                                oracle.bc(g.row_offsets, g.col_indices, srcs), rtol=BC_TOL, atol=0)
     with pytest.raises(RuntimeError):
         grx.bc_multi(dg, list(range(65)))
+
+
+def test_bc_multi_isolated_source_lane_and_sssp_zero_weights(grx, loaded):
+    g, dg = GRAPHS["disconnected"], loaded["disconnected"]
+    srcs = [0, 1, 5, 0, 12]                              # vertex 0 is isolated
+    np.testing.assert_allclose(grx.bc_multi(dg, srcs).cpu().numpy(),
+                               oracle.bc(g.row_offsets, g.col_indices, srcs), rtol=BC_TOL, atol=0)
+    # near-far bands with zero-weight edges
+    h = inputs.rmat_graph(11, 8, seed=21)
+    rows = np.repeat(np.arange(h.nv), np.diff(h.row_offsets))
+    lo = np.minimum(rows, h.col_indices).astype(np.uint64)
+    hi = np.maximum(rows, h.col_indices).astype(np.uint64)
+    h.weights = (inputs.draw(31, lo * np.uint64(h.nv) + hi) % np.uint64(4)).astype(np.uint32)
+    dh = grx.load(h, validate=True)
+    for s in _sources(h, 3, seed=4):
+        want = oracle.sssp(h.row_offsets, h.col_indices, h.weights, s)
+        for delta in (0, 1, 2):
+            assert np.array_equal(grx.as_uint32(grx.sssp(dh, s, opts=grx.opts(sssp_delta=delta))), want), delta
