@@ -223,6 +223,21 @@ def _captured_traffic(workload: str):
     return None
 
 
+def world_rate(units: float, seconds: float, device="cpu"):
+    """Whole-job rate over the default process group: the units all ranks
+    processed / the slowest rank's time.  Returns (rate, max seconds); a
+    single process (no group) gets units / seconds."""
+    import torch
+    import torch.distributed as dist
+    if not (dist.is_available() and dist.is_initialized()) or dist.get_world_size() == 1:
+        return units / seconds, seconds
+    tmax = torch.tensor([seconds], dtype=torch.float64, device=device)
+    dist.all_reduce(tmax, op=dist.ReduceOp.MAX)
+    tot = torch.tensor([units], dtype=torch.float64, device=device)
+    dist.all_reduce(tot, op=dist.ReduceOp.SUM)
+    return float(tot.item()) / float(tmax.item()), float(tmax.item())
+
+
 def _dist_env():
     ws = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
@@ -421,12 +436,8 @@ def main():
     edges_total = sum(per_src[s]["edges"] for s in order)
     bytes_total = sum(per_src[s]["bytes"] for s in order)
     t_total = sum(step_ms) / 1e3
-    t_max = t_total
-    if ws > 1:
-        t = torch.tensor([t_total], dtype=torch.float64, device=f"cuda:{dev}")
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        t_max = float(t.item())
-    gteps = edges_total * ws / t_max / 1e9
+    rate, t_max = world_rate(float(edges_total), t_total, device=f"cuda:{dev}")
+    gteps = rate / 1e9
     peak, peak_kind = _peaks()
     achieved = bytes_total / (sum(kern_ms) / 1e3) / 1e9
 

@@ -78,7 +78,10 @@ struct BcmWarpSmem {
     int32_t u[BCM_WTILE + 1];
     unsigned long long f[BCM_WTILE + 1];
     alignas(16) uint16_t rid[BCM_WTILE];
-    DagEntry dag[BCM_WTILE];
+    union {
+        DagEntry dag[BCM_WTILE];        // edge phases: the tile's shortest-path edges
+        uint16_t list[32 * 32];         // finalize: compacted bits of a 32-word chunk
+    };
 };
 
 __device__ __forceinline__ unsigned long long *hist_level(const BcmArgs<int32_t> &a, int k) {
@@ -428,7 +431,7 @@ __global__ void __launch_bounds__(BCM_BLOCK) k_bcm_persistent(BcmArgs<OffT> a) {
             }
             level_edges<OffT, true>(a, st, w, lane_edges);
         } else if (st.op == MOP_FINAL) {
-            forward_final<OffT>(a, st, reinterpret_cast<uint16_t *>(w.dag));
+            forward_final<OffT>(a, st, w.list);
         } else if (st.op == MOP_FIN_BUILD) {
             finish_and_build<OffT>(a, st);
         } else {
