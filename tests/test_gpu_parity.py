@@ -548,6 +548,9 @@ def test_bc_multi_isolated_source_lane_and_sssp_zero_weights(grx, loaded):
     srcs = [0, 1, 5, 0, 12]                              # vertex 0 is isolated
     np.testing.assert_allclose(grx.bc_multi(dg, srcs).cpu().numpy(),
                                oracle.bc(g.row_offsets, g.col_indices, srcs), rtol=BC_TOL, atol=0)
+    de = grx.load(inputs.csr_from_edges(40, []))         # no edges at all
+    assert np.all(grx.bc_multi(de, [0, 3, 39]).cpu().numpy() == 0)
+    grx.graph_status(de)
     # near-far bands with zero-weight edges
     h = inputs.rmat_graph(11, 8, seed=21)
     rows = np.repeat(np.arange(h.nv), np.diff(h.row_offsets))
