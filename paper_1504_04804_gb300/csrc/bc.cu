@@ -17,9 +17,10 @@
 //    d + 1) is a shortest-path edge: sigma[u] is added to sigma[w] (float64
 //    reduction).  Small levels claim w by clearing its code bits (atomic AND;
 //    the lane that saw 3 appends w).  Levels with at least push_bitmap * V
-//    edges only OR w's bit into a next-level bitmap (no returned atomics);
-//    a second phase, by warps owning 32-word chunks of it, writes the new
-//    codes, appends the vertices in vertex order and clears the bitmap.
+//    edges only add the path counts (no claim, no returned atomics): after
+//    the barrier the unreached vertices with a nonzero count are exactly the
+//    new level, and warps owning 32-word chunks of the vertices find them,
+//    write their codes and append them in vertex order.
 //  * Backward, level k from the deepest one up, one phase per level: every
 //    vertex v of level k sums coef[w] = (1 + delta[w]) / sigma[w] over its
 //    neighbours w at depth k + 1 (a pull: no atomic per edge, so a hub with
@@ -72,7 +73,6 @@ struct BcArgs {
     const OffT *ro;
     const int32_t *col;
     uint32_t *code;            // 2-bit level codes, 16 vertices per word (3 = unreached)
-    uint32_t *F;               // next-level bitmap of bitmap levels
     double *sigma;
     double *acc;               // backward: row sums, then coef of finished vertices
     int32_t *fix;              // backward: vertices whose rows crossed tiles
@@ -130,6 +130,16 @@ __device__ __forceinline__ uint32_t spread16(uint32_t x) {
     x = (x | (x << 4)) & 0x0f0f0f0fu;
     x = (x | (x << 2)) & 0x33333333u;
     x = (x | (x << 1)) & 0x55555555u;
+    return x;
+}
+
+// Even bits of x's 2-bit fields that equal 3 (unreached), packed into 16 bits.
+__device__ __forceinline__ uint32_t unreached16(uint32_t x) {
+    x = x & (x >> 1) & 0x55555555u;
+    x = (x | (x >> 1)) & 0x33333333u;
+    x = (x | (x >> 2)) & 0x0f0f0f0fu;
+    x = (x | (x >> 4)) & 0x00ff00ffu;
+    x = (x | (x >> 8)) & 0x0000ffffu;
     return x;
 }
 
@@ -231,10 +241,7 @@ __device__ void forward_level(const BcArgs<OffT> &a, const BcState &st, BcWarpSm
         if (BMP) {
 #pragma unroll
             for (int k = 0; k < BC_ITEMS; ++k) {
-                if (c[k] == 3u) {                                // codes do not change in this phase
-                    atomicAdd(a.sigma + v[k], su[k]);           // results unused: reductions
-                    atomicOr(a.F + (v[k] >> 5), 1u << (v[k] & 31));
-                }
+                if (c[k] == 3u) atomicAdd(a.sigma + v[k], su[k]);   // codes fixed in this phase; reduction
             }
         } else {
             uint32_t claimed = 0, dag = 0;
@@ -272,9 +279,10 @@ __device__ void forward_level(const BcArgs<OffT> &a, const BcState &st, BcWarpSm
     }
 }
 
-// Second phase of a bitmap level: the owner of each 32-word chunk of F writes
-// its vertices' codes (d + 1 mod 3), appends them (with edges) to level d + 1
-// in vertex order and clears the chunk.
+// Second phase of a bitmap level: per 32-word chunk of vertices, the
+// unreached ones whose path count became nonzero form level d + 1; the owner
+// writes their codes (d + 1 mod 3) and appends them (with edges) in vertex
+// order.  The warp reads the chunk's path counts word by word (coalesced).
 template <typename OffT>
 __device__ void forward_final(const BcArgs<OffT> &a, const BcState &st, uint16_t *list) {
     const int d = st.d;
@@ -288,9 +296,19 @@ __device__ void forward_final(const BcArgs<OffT> &a, const BcState &st, uint16_t
     const int64_t nwarps = (int64_t)gridDim.x * BC_WARPS;
     for (int64_t sc = (int64_t)blockIdx.x * BC_WARPS + (threadIdx.x >> 5); sc < nsc; sc += nwarps) {
         const int64_t wd = sc * 32 + lane;
-        const uint32_t bits = wd < a.words ? __ldcg(a.F + wd) : 0u;
+        uint32_t cand = 0u;
+        if (wd < a.words)
+            cand = (unreached16(__ldcg(a.code + 2 * wd)) | (unreached16(__ldcg(a.code + 2 * wd + 1)) << 16)) &
+                   __ldg(a.nz + wd);
+        uint32_t bits = 0u;
+#pragma unroll 8
+        for (int j = 0; j < 32; ++j) {
+            const uint32_t cj = __shfl_sync(GRX_FULL_MASK, cand, j);
+            const bool hit = ((cj >> lane) & 1u) && __ldcg(a.sigma + ((sc * 32 + j) * 32 + lane)) != 0.0;
+            const uint32_t b = __ballot_sync(GRX_FULL_MASK, hit);
+            if ((int)lane == j) bits = b;
+        }
         if (bits) {
-            a.F[wd] = 0u;
 #pragma unroll
             for (int h = 0; h < 2; ++h) {
                 const uint32_t half = (bits >> (16 * h)) & 0xffffu;
@@ -438,15 +456,6 @@ __device__ void backward_level(const BcArgs<OffT> &a, const BcState &st, BcWarpS
     }
 }
 
-// Even bits of x's 2-bit fields that equal 3 (unreached), packed into 16 bits.
-__device__ __forceinline__ uint32_t unreached16(uint32_t x) {
-    x = x & (x >> 1) & 0x55555555u;
-    x = (x | (x >> 1)) & 0x33333333u;
-    x = (x | (x >> 2)) & 0x0f0f0f0fu;
-    x = (x | (x >> 4)) & 0x00ff00ffu;
-    x = (x | (x >> 8)) & 0x0000ffffu;
-    return x;
-}
 
 // Forward pull of level d: the owner of each 32-word chunk sums, for every
 // unreached non-isolated vertex of the chunk, sigma over its neighbours at
@@ -791,7 +800,6 @@ grx_status launch_typed(grx_graph *g, const int32_t *srcs, int n, double *bc_out
     a.ro = (const OffT *)g->ro;
     a.col = g->col;
     a.code = g->bc_code;
-    a.F = g->fbits[1];
     a.sigma = g->bc_sigma;
     a.acc = g->bc_acc;
     a.fix = g->ulist[0];
@@ -825,7 +833,6 @@ grx_status launch_typed(grx_graph *g, const int32_t *srcs, int n, double *bc_out
     for (int i = 0; i < n; ++i) {
         a.src = srcs[i];
         GRX_CUDA(cudaMemsetAsync(a.code, 0xff, (size_t)g->words * 8, s));
-        GRX_CUDA(cudaMemsetAsync(a.F, 0, (size_t)g->words * 4, s));
         GRX_CUDA(cudaMemsetAsync(a.sigma, 0, nv * 8, s));
         GRX_CUDA(cudaMemsetAsync(a.acc, 0, nv * 8, s));
         k_bc_init<OffT><<<1, 1, 0, s>>>(a.src, a.ro, a.code, a.sigma, a.Q, a.E, a.R, g->ctl);
