@@ -70,3 +70,78 @@ def test_bc_multi_at_scale_22(big):
     got = grx.bc_multi(g, lanes).cpu().numpy()
     grx.graph_status(g)
     np.testing.assert_allclose(got, oracle.bc(ro, col, lanes), rtol=1e-9, atol=0)
+
+
+# ---- the other benchmarked configurations at full size
+
+def test_bfs_rmat16_sixteen_sources():
+    """R-MAT scale 16 (65,536 vertices): plain BFS from the 16 seeded sources, bit-exact."""
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    build.build()
+    from paper_1504_04804_gb300 import grx
+    g = inputs.rmat_graph(16, 16, seed=16)
+    dg = grx.load(g)
+    for s in inputs.pick_sources(g.row_offsets, 16, 1):
+        for mode in (0, 1):
+            assert np.array_equal(grx.bfs(dg, int(s), opts=grx.opts(direction=mode)).cpu().numpy(),
+                                  oracle.bfs(g.row_offsets, g.col_indices, int(s))), (int(s), mode)
+
+
+def test_grid_4096_bfs_loops_and_sssp():
+    """The 4096 x 4096 grid (10 % of edges deleted, weights U[1,1000]): BFS with
+    the three level loops and SSSP (plain and near-far) from a bench source."""
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    build.build()
+    from paper_1504_04804_gb300 import autotune, grx
+    ro, col, w = grx.grid_graph_device(4096, 4096, p_del=0.1, seed=4096, wmax=1000, weight_seed=4196)
+    g = grx.graph_load_csr(ro, col, w)
+    roh, colh, wh = ro.cpu().numpy().astype(np.int64), col.cpu().numpy(), w.cpu().numpy().view(np.uint32)
+    s = int(inputs.pick_sources(roh, 4, 1)[0])
+    want = oracle.bfs(roh, colh, s)
+    for loop in (grx.GRX_LOOP_PERSISTENT, grx.GRX_LOOP_HOST, grx.GRX_LOOP_GRAPH):
+        assert np.array_equal(grx.bfs(g, s, opts=grx.opts(loop=loop)).cpu().numpy(), want), loop
+    dist = oracle.sssp(roh, colh, wh, s)
+    tuned = autotune.tune_sssp_delta(g, roh, wh, cache=None)
+    for delta in (0, 20000, tuned["sssp_delta"]):
+        assert np.array_equal(grx.as_uint32(grx.sssp(g, s, opts=grx.opts(sssp_delta=delta))), dist), delta
+    grx.graph_status(g)
+
+
+def test_rmat26_dobfs_multi_source_and_pagerank_step():
+    """R-MAT scale 26 with int64 offsets, as the benchmark loads it: one
+    DOBFS source and two of the 64 multi-source lanes bit-exact against the
+    oracle (the other lanes against single-source BFS on the GPU); PageRank:
+    the 20th iteration recomputed in float64 at 256 seeded vertices from the
+    GPU's 19th, within 1e-5, and the ranks summing to 1."""
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    if torch.cuda.mem_get_info()[0] < 60e9:
+        pytest.skip("needs 60 GB of free device memory")
+    build.build()
+    from paper_1504_04804_gb300 import grx
+    ro, col, _ = grx.rmat_graph_device(26, 16, seed=26)
+    g = grx.graph_load_csr(ro, col, None, offsets64=True)
+    roh, colh = ro.cpu().numpy().astype(np.int64), col.cpu().numpy()
+    src = int(inputs.pick_sources(roh, 16, 1)[0])
+    assert np.array_equal(grx.bfs(g, src).cpu().numpy(), oracle.bfs(roh, colh, src))
+    lanes = [int(x) for x in inputs.pick_sources(roh, 64, 5)]
+    d = grx.bfs_multi(g, lanes)
+    for b in (0, 63):
+        assert np.array_equal(d[b].cpu().numpy(), oracle.bfs(roh, colh, lanes[b])), b
+    for b in range(1, 63, 7):
+        assert torch.equal(d[b], grx.bfs(g, lanes[b])), b
+    del d
+    r19 = grx.pagerank(g, 0.85, 19).cpu().numpy().astype(np.float64)
+    r20 = grx.pagerank(g, 0.85, 20).cpu().numpy().astype(np.float64)
+    assert abs(r20.sum() - 1.0) < 1e-3
+    nv = roh.shape[0] - 1
+    deg = np.diff(roh)
+    dangling = r19[deg == 0].sum()
+    rng = np.random.default_rng(26)
+    for v in rng.choice(np.flatnonzero(deg > 0), size=256, replace=False):
+        nb = colh[roh[v]:roh[v + 1]]
+        want = (1 - 0.85) / nv + 0.85 * (np.sum(r19[nb] / deg[nb]) + dangling / nv)
+        assert abs(r20[v] - want) <= 1e-5 * want, int(v)
+    grx.graph_status(g)
