@@ -54,6 +54,7 @@ def test_opts_struct_layout_matches_defaults(libgrx):
     assert o.direction == grx.GRX_DIR_AUTO
     assert abs(o.alpha - 0.01) < 1e-7 and abs(o.beta - 0.1) < 1e-7
     assert o.loop == grx.GRX_LOOP_PERSISTENT and o.timeout_s == 5.0
+    assert o.push_bitmap == 0.0 and o.sssp_delta == 0      # library defaults: V/8 rule, no bands
 
 
 def test_argument_errors_without_gpu():
@@ -65,6 +66,10 @@ def test_argument_errors_without_gpu():
     assert lib.sssp(None, 0, None, None, None) == grx.GRX_EINVAL
     assert lib.cc(None, None, None) == grx.GRX_EINVAL
     assert lib.pagerank(None, 0.85, 20, None, None) == grx.GRX_EINVAL
+    assert lib.bc(None, None, 1, None, None, None, None) == grx.GRX_EINVAL
+    assert lib.bc_multi(None, None, 1, None, None, None) == grx.GRX_EINVAL
+    assert lib.bfs_multi(None, None, 1, None, None, None) == grx.GRX_EINVAL
+    assert lib.sssp_multi(None, None, 1, None, None, None) == grx.GRX_EINVAL
     out = ctypes.c_void_p()
     assert lib.graph_load_csr(None, 4, 0, None, 0, None, None, 0, None, ctypes.byref(out)) == grx.GRX_EINVAL
     assert lib.grx_rmat_edges(0, 10, 1, 0, 0, 0, None, None, None) == grx.GRX_EINVAL
