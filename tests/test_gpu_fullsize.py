@@ -5,6 +5,8 @@ launch configuration.  Every primitive is compared with the CPU oracle on
 seeded sources of the benchmark's own source list: BFS depths, SSSP
 distances and CC labels bit-exact, PageRank within 1e-5 relative, BC within
 1e-9 relative, and two lanes of a 64-lane multi-source BFS."""
+import os
+
 import numpy as np
 import pytest
 
@@ -109,10 +111,26 @@ def test_grid_4096_bfs_loops_and_sssp():
     grx.graph_status(g)
 
 
+def check_lanes_parallel(ro, col, lanes, row_of, chunk=16):
+    """oracle.check_bfs on every lane, `chunk` lanes at a time on host
+    threads (the oracle's C calls release the GIL); row_of(b) gives lane b's
+    depths as a host array.  Returns the violation count of each lane."""
+    from concurrent.futures import ThreadPoolExecutor
+    counts = []
+    with ThreadPoolExecutor(max_workers=min(chunk, os.cpu_count() or 1)) as pool:
+        for b0 in range(0, len(lanes), chunk):
+            idx = range(b0, min(len(lanes), b0 + chunk))
+            rows = [row_of(b) for b in idx]
+            counts += list(pool.map(lambda br: oracle.check_bfs(ro, col, lanes[br[0]], br[1]),
+                                    zip(idx, rows)))
+    return counts
+
+
 def test_rmat26_dobfs_multi_source_and_pagerank_step():
     """R-MAT scale 26 with int64 offsets, as the benchmark loads it: one
     DOBFS source and two of the 64 multi-source lanes bit-exact against the
-    oracle (the other lanes against single-source BFS on the GPU); PageRank:
+    oracle, every lane against the BFS invariants on host threads, and nine
+    lanes against single-source BFS on the GPU; PageRank:
     the 20th iteration recomputed in float64 at 256 seeded vertices from the
     GPU's 19th, within 1e-5, and the ranks summing to 1."""
     if not torch.cuda.is_available():
@@ -132,6 +150,8 @@ def test_rmat26_dobfs_multi_source_and_pagerank_step():
         assert np.array_equal(d[b].cpu().numpy(), oracle.bfs(roh, colh, lanes[b])), b
     for b in range(1, 63, 7):
         assert torch.equal(d[b], grx.bfs(g, lanes[b])), b
+    # every lane against the BFS invariants (multithreaded host checker)
+    assert check_lanes_parallel(roh, colh, lanes, lambda b: d[b].cpu().numpy()) == [0] * 64
     del d
     r19 = grx.pagerank(g, 0.85, 19).cpu().numpy().astype(np.float64)
     r20 = grx.pagerank(g, 0.85, 20).cpu().numpy().astype(np.float64)
