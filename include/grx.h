@@ -190,19 +190,20 @@ grx_status sssp_multi(grx_graph *g, const int32_t *srcs_host, int n, uint32_t *d
  * The graph must be symmetric (undirected, as every graph of Sec. 7).
  * Float64 arithmetic; reductions arrive in any order, so values match a
  * sequential float64 sum to rounding.  Forward levels with at least
- * opts->push_bitmap * nv edges mark the next level in a bitmap instead of
- * claiming vertices one by one (results do not depend on it).
- * opts->direction: GRX_DIR_AUTO picks per level by edge counts -- a forward
- * level is a pull over the unreached vertices when they have less than a
- * quarter of the frontier's edges, a backward level pushes from the level below when that
- * one has fewer edges; GRX_DIR_PUSH keeps forward push / backward pull,
- * GRX_DIR_PULL the other way round (after the source level).  Uses about
- * 16 bytes of workspace per vertex.  With opts->collect_stats, grx_last_stats describes the last
+ * opts->push_bitmap * nv edges only add path counts and find the next level
+ * afterwards from the nonzero counts, instead of claiming vertices one by
+ * one (results do not depend on it).  opts->direction: GRX_DIR_AUTO picks
+ * per level by edge counts -- a forward level is a pull over the unreached
+ * vertices when they have less than a quarter of the frontier's edges, a
+ * backward level pushes from the level below when that one has fewer edges;
+ * GRX_DIR_PUSH keeps forward push / backward pull, GRX_DIR_PULL the other
+ * way round (after the source level).  Uses about 16 bytes of workspace per
+ * vertex.  With opts->collect_stats, grx_last_stats describes the last
  * source's phases: forward levels (dir 0) then backward levels (dir 1),
  * frontier = the level's vertices, edges_examined = the edges the phase
  * reads (a forward pull: the unreached vertices' rows; a backward push: the
  * rows of the level below), vertices_scanned = the phase's kind.
- * Bad source or NULL output -> GRX_EINVAL. */
+ * Bad source, n < 1, bad direction or NULL output -> GRX_EINVAL. */
 grx_status bc(grx_graph *g, const int32_t *srcs_host, int n, double *bc_out, double *sigma_out,
               const grx_opts *opts, void *stream);
 
@@ -213,7 +214,11 @@ grx_status bc(grx_graph *g, const int32_t *srcs_host, int n, double *bc_out, dou
  * traversal).  bc_out: device float64[nv], overwritten.  Needs about
  * 1,040 + 8 * GRX_BCM_MAX_LEVELS bytes of workspace per vertex (allocated on
  * first use).  Graphs deeper than GRX_BCM_MAX_LEVELS - 1 levels set
- * GRX_ERANGE (use bc() there).  The graph must be symmetric. */
+ * GRX_ERANGE status (reported by grx_graph_status; use bc() there).  The
+ * graph must be symmetric.  With opts->collect_stats, grx_last_stats lists
+ * the phases (dir 0 forward, 1 backward), vertices_scanned = the
+ * (edge, lane) pairs on shortest paths the phase updated.  n outside 1..64,
+ * a bad source or NULL output -> GRX_EINVAL. */
 #define GRX_BCM_MAX_LEVELS 16
 grx_status bc_multi(grx_graph *g, const int32_t *srcs_host, int n, double *bc_out, const grx_opts *opts,
                     void *stream);
