@@ -285,11 +285,16 @@ int oracle_bc(int64_t nv, const int64_t *row_offsets, const int32_t *col_indices
 /* returns the number of violations found (0 = valid), or a negative error.  */
 /* ------------------------------------------------------------------------ */
 
-/* BFS depths: depth[src]==0; on every edge (u,v) either both ends are
- * unreached or both reached with |depth[u]-depth[v]| <= 1; every reached
- * v != src has a neighbour at depth[v]-1.  If parent != NULL, parent[v] must be
- * a neighbour of v at depth[v]-1 for reached v != src, parent[src]==src, and
- * -1 for unreached v. */
+/* BFS depths: depth[src]==0 and no other vertex has depth 0; on every edge
+ * (u,v) either both ends are unreached or both reached with
+ * |depth[u]-depth[v]| <= 1; every reached v != src has a neighbour at
+ * depth[v]-1.  Together these fix the depths uniquely: following
+ * predecessors from any reached vertex descends one level per step and can
+ * only end at the one depth-0 vertex, the source, so depth[v] is the length
+ * of a path from src (>= the hop distance); and the +-1 rule along a
+ * shortest path bounds it by the hop distance.  If parent != NULL,
+ * parent[v] must be a neighbour of v at depth[v]-1 for reached v != src,
+ * parent[src]==src, and -1 for unreached v. */
 int64_t oracle_check_bfs(int64_t nv, const int64_t *row_offsets, const int32_t *col_indices,
                          int32_t src, const int32_t *depth, const int32_t *parent)
 {
@@ -299,6 +304,7 @@ int64_t oracle_check_bfs(int64_t nv, const int64_t *row_offsets, const int32_t *
     for (int64_t v = 0; v < nv; ++v) {
         int32_t dv = depth[v];
         if (dv < -1) { ++bad; continue; }
+        if (dv == 0 && v != src) ++bad;          /* a second root */
         int has_pred = 0, parent_ok = 0;
         for (int64_t e = row_offsets[v]; e < row_offsets[v + 1]; ++e) {
             int32_t u = col_indices[e];
@@ -322,8 +328,14 @@ int64_t oracle_check_bfs(int64_t nv, const int64_t *row_offsets, const int32_t *
 }
 
 /* SSSP distances: dist[src]==0; dist[v] <= dist[u] + w(u,v) on every edge
- * (triangle inequality, in uint64); every reached v != src has a tight edge
- * dist[v] == dist[u] + w(u,v); an unreached vertex has no reached neighbour. */
+ * (triangle inequality, in uint64); an unreached vertex has no reached
+ * neighbour; and every reached vertex is reachable from src along tight
+ * edges (dist[v] == dist[u] + w(u,v)), found by a FIFO sweep from src over
+ * tight edges.  The sweep makes each dist[v] the length of a real path
+ * (>= the shortest distance) and the triangle inequality along a shortest
+ * path bounds it from above, so the distances are the shortest ones.  A
+ * local "has a tight edge" test would not do: with zero weights a component
+ * away from src could carry distance 0 throughout. */
 int64_t oracle_check_sssp(int64_t nv, const int64_t *row_offsets, const int32_t *col_indices,
                           const uint32_t *weights, int32_t src, const uint32_t *dist)
 {
@@ -331,34 +343,70 @@ int64_t oracle_check_sssp(int64_t nv, const int64_t *row_offsets, const int32_t 
     int64_t bad = 0;
     if (dist[src] != 0) ++bad;
     for (int64_t v = 0; v < nv; ++v) {
-        int tight = 0;
         for (int64_t e = row_offsets[v]; e < row_offsets[v + 1]; ++e) {
             int32_t u = col_indices[e];
             /* edge (v,u) with weight w: the undirected weight is the same both ways */
             if (dist[u] == UINT32_MAX) { if (dist[v] != UINT32_MAX) ++bad; continue; }
             uint64_t via = (uint64_t)dist[u] + weights[e];
             if (dist[v] == UINT32_MAX || (uint64_t)dist[v] > via) ++bad;
-            if ((uint64_t)dist[v] == via) tight = 1;
         }
-        if (v != src && dist[v] != UINT32_MAX && !tight) ++bad;
     }
+    if (dist[src] != 0) return bad;
+    /* tight-edge reachability from src */
+    uint8_t *seen = (uint8_t *)calloc((size_t)nv, 1);
+    int32_t *queue = (int32_t *)malloc(sizeof(int32_t) * (size_t)nv);
+    if (!seen || !queue) { free(seen); free(queue); return OR_ENOMEM; }
+    int64_t head = 0, tail = 0;
+    seen[src] = 1;
+    queue[tail++] = src;
+    while (head < tail) {
+        int32_t u = queue[head++];
+        for (int64_t e = row_offsets[u]; e < row_offsets[u + 1]; ++e) {
+            int32_t v = col_indices[e];
+            if (!seen[v] && dist[v] != UINT32_MAX &&
+                (uint64_t)dist[v] == (uint64_t)dist[u] + weights[e]) {
+                seen[v] = 1;
+                queue[tail++] = v;
+            }
+        }
+    }
+    for (int64_t v = 0; v < nv; ++v)
+        if (dist[v] != UINT32_MAX && !seen[v]) ++bad;
+    free(seen);
+    free(queue);
     return bad;
 }
 
-/* CC labels: equal across every edge; label[v] <= v; label[label[v]] ==
- * label[v] (the label is a member of its own class and is that class's
- * representative). */
+/* CC labels: label[v] must be the smallest vertex id of v's connected
+ * component.  The components are found here by FIFO sweeps (a method other
+ * than the union-find of oracle_cc): vertices are taken in increasing id
+ * order, and each one not yet swept starts a sweep of its whole component, so
+ * it is that component's minimum; every vertex the sweep reaches must carry
+ * it as its label.  This rejects wrong representatives and merged or split
+ * components alike. */
 int64_t oracle_check_cc(int64_t nv, const int64_t *row_offsets, const int32_t *col_indices,
                         const int32_t *label)
 {
     if (nv <= 0) return OR_EINVAL;
+    uint8_t *seen = (uint8_t *)calloc((size_t)nv, 1);
+    int32_t *queue = (int32_t *)malloc(sizeof(int32_t) * (size_t)nv);
+    if (!seen || !queue) { free(seen); free(queue); return OR_ENOMEM; }
     int64_t bad = 0;
-    for (int64_t v = 0; v < nv; ++v) {
-        int32_t l = label[v];
-        if (l < 0 || (int64_t)l > v) { ++bad; continue; }
-        if (label[l] != l) ++bad;
-        for (int64_t e = row_offsets[v]; e < row_offsets[v + 1]; ++e)
-            if (label[col_indices[e]] != l) ++bad;
+    for (int64_t r = 0; r < nv; ++r) {
+        if (seen[r]) continue;
+        int64_t head = 0, tail = 0;
+        seen[r] = 1;
+        queue[tail++] = (int32_t)r;
+        while (head < tail) {
+            int32_t u = queue[head++];
+            if ((int64_t)label[u] != r) ++bad;
+            for (int64_t e = row_offsets[u]; e < row_offsets[u + 1]; ++e) {
+                int32_t v = col_indices[e];
+                if (!seen[v]) { seen[v] = 1; queue[tail++] = v; }
+            }
+        }
     }
+    free(seen);
+    free(queue);
     return bad;
 }

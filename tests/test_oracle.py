@@ -322,6 +322,92 @@ def test_checkers_reject_planted_mistakes():
     assert oracle.check_cc(g.row_offsets, g.col_indices, bad) > 0
 
 
+def test_checkers_reject_a_second_root_and_merged_components():
+    """Mistakes a purely local check misses: a second depth-0 vertex (it
+    needs no predecessor), a zero-weight island away from the source carrying
+    distance 0 (every edge in it is tight), and two components merged under
+    one label (labels agree across every edge)."""
+    star = inputs.csr_from_edges(5, [(0, 1), (0, 2), (0, 3), (0, 4)])
+    d = oracle.bfs(star.row_offsets, star.col_indices, 0)
+    assert oracle.check_bfs(star.row_offsets, star.col_indices, 0, d) == 0
+    bad = d.copy()
+    bad[3] = 0
+    assert oracle.check_bfs(star.row_offsets, star.col_indices, 0, bad) > 0
+    # an unreached pair labelled as if it held its own source
+    two = inputs.csr_from_edges(4, [(0, 1), (2, 3)])
+    d = oracle.bfs(two.row_offsets, two.col_indices, 0)
+    bad = d.copy()
+    bad[2], bad[3] = 0, 1
+    assert oracle.check_bfs(two.row_offsets, two.col_indices, 0, bad) > 0
+    w = np.array([5, 5, 0, 0], dtype=np.uint32)          # rows 0,1,2,3: edge 2-3 weighs 0
+    dist = oracle.sssp(two.row_offsets, two.col_indices, w, 0)
+    assert oracle.check_sssp(two.row_offsets, two.col_indices, w, 0, dist) == 0
+    bad = dist.copy()
+    bad[2] = bad[3] = 0
+    assert oracle.check_sssp(two.row_offsets, two.col_indices, w, 0, bad) > 0
+    lab = oracle.cc(two.row_offsets, two.col_indices)
+    assert list(lab) == [0, 0, 2, 2]
+    assert oracle.check_cc(two.row_offsets, two.col_indices, lab) == 0
+    assert oracle.check_cc(two.row_offsets, two.col_indices, np.zeros(4, np.int32)) > 0
+    # one component split in two
+    path = inputs.csr_from_edges(4, [(0, 1), (1, 2), (2, 3)])
+    assert oracle.check_cc(path.row_offsets, path.col_indices, np.array([0, 0, 2, 2], np.int32)) > 0
+
+
+N4 = 4
+PAIRS4 = list(itertools.combinations(range(N4), 2))
+
+
+def _graphs4():
+    for mask in range(1 << len(PAIRS4)):
+        yield mask, [PAIRS4[i] for i in range(len(PAIRS4)) if mask >> i & 1]
+
+
+def _fw4(edges, wmap=None):
+    d = np.full((N4, N4), np.inf)
+    np.fill_diagonal(d, 0)
+    for a, b in edges:
+        d[a, b] = d[b, a] = 1.0 if wmap is None else wmap[(a, b)]
+    for k in range(N4):
+        d = np.minimum(d, d[:, k:k + 1] + d[k:k + 1, :])
+    return d
+
+
+def test_checkers_accept_exactly_the_right_answer_on_every_4_vertex_graph():
+    """Brute force: on every labelled 4-vertex graph, among all candidate
+    answers (BFS depths in {-1..3}^4, CC labels in {0..3}^4, SSSP distances
+    in {0..6, inf}^4 with weights in {0,1,2}), the checkers accept exactly one,
+    the Floyd-Warshall / transitive-closure answer.  So the invariants are
+    complete, not merely necessary."""
+    depth_cands = [np.array(c, dtype=np.int32) for c in itertools.product(range(-1, 4), repeat=N4)]
+    label_cands = [np.array(c, dtype=np.int32) for c in itertools.product(range(N4), repeat=N4)]
+    inf = 0xFFFFFFFF
+    dist_cands = [np.array(c, dtype=np.uint32)
+                  for c in itertools.product([0, 1, 2, 3, 4, 5, 6, inf], repeat=N4)]
+    rng = np.random.default_rng(44)
+    for mask, edges in _graphs4():
+        g = inputs.csr_from_edges(N4, edges)
+        fw = _fw4(edges)
+        src = mask % N4
+        want = np.where(np.isinf(fw[src]), -1, fw[src]).astype(np.int32)
+        ok = [c for c in depth_cands if oracle.check_bfs(g.row_offsets, g.col_indices, src, c) == 0]
+        assert len(ok) == 1 and np.array_equal(ok[0], want), (mask, src)
+        reach = np.isfinite(fw)
+        want_l = np.array([np.flatnonzero(reach[v]).min() for v in range(N4)], dtype=np.int32)
+        ok = [c for c in label_cands if oracle.check_cc(g.row_offsets, g.col_indices, c) == 0]
+        assert len(ok) == 1 and np.array_equal(ok[0], want_l), mask
+        wmap = {}
+        for a, b in edges:
+            wmap[(a, b)] = wmap[(b, a)] = int(rng.integers(0, 3))
+        rows = np.repeat(np.arange(N4), np.diff(g.row_offsets))
+        w = np.array([wmap[(int(r), int(c))] for r, c in zip(rows, g.col_indices)], dtype=np.uint32)
+        fww = _fw4(edges, wmap)
+        want_d = np.where(np.isinf(fww[src]), inf, fww[src]).astype(np.uint32)
+        ok = [c for c in dist_cands
+              if oracle.check_sssp(g.row_offsets, g.col_indices, w, src, c) == 0]
+        assert len(ok) == 1 and np.array_equal(ok[0], want_d), (mask, src, wmap)
+
+
 def test_rmat_generator_shape():
     scale, ef = 12, 16
     u, v = inputs.rmat_edges(scale, ef, seed=12)
