@@ -259,14 +259,18 @@ grx_status grx_pagerank_block(grx_graph *g, int shift);
  *   status_out   int32[1] or NULL: receives the device-side status of this
  *                call (0, or GRX_ETIMEOUT if a bounded wait ran out)
  * All traversal scratch lives in one fixed __device__ array sized for
- * GRX_NOALLOC_MAX_NV vertices (about 17 MB), which every GPU that loads the
- * library holds until the process exits.  nv above that limit returns
- * GRX_ERANGE; ne must be below 2^31.  opts as for bfs (collect_stats must be 0).
+ * GRX_NOALLOC_MAX_NV vertices (GRX_NOALLOC_SCRATCH_BYTES, about 19.2 MB),
+ * which every GPU that loads the library holds until the process exits.  nv
+ * above that limit returns GRX_ERANGE; ne must be below 2^31.  opts as for
+ * bfs, except that collect_stats must be 0 and loop must be
+ * GRX_LOOP_PERSISTENT or GRX_LOOP_HOST: GRX_LOOP_GRAPH (which instantiates a
+ * CUDA graph and allocates its argument block) returns GRX_EINVAL.
  * The first call on a device looks up the array's device address (once per
  * device, with that device current); make that first call before any CUDA
  * stream capture.  Every call shares the array and clears what it needs;
  * calls whose GPU work overlaps race on it, so order them (one stream). */
 #define GRX_NOALLOC_MAX_NV (1 << 19)
+#define GRX_NOALLOC_SCRATCH_BYTES 19219328
 grx_status bfs_noalloc(int64_t nv, int64_t ne, const int32_t *row_offsets,
                        const int32_t *col_indices, int32_t src, int32_t *depth_out,
                        int32_t *parent_out, int32_t *status_out, const grx_opts *opts,

@@ -8,7 +8,7 @@
 // path that may not fail with out-of-memory half-way.  bfs_noalloc serves
 // them: the caller passes the CSR arrays and the output arrays (all device
 // memory it owns), and every piece of traversal scratch -- frontier queues,
-// bitmaps, unvisited lists, the control block -- lives in one file-scope
+// bitmaps, the control block -- lives in one file-scope
 // __device__ array of fixed size, reserved when the library is loaded and held
 // by every GPU that loads it until the process exits.
 //
@@ -35,8 +35,9 @@ struct NoallocScratch {
     int32_t qv[3][kMaxNv];
     uint32_t qe[3][kMaxNv];
     int32_t qr[3][kMaxNv];
-    int32_t ulist[2][kMaxNv];
 };
+static_assert(sizeof(NoallocScratch) == GRX_NOALLOC_SCRATCH_BYTES,
+              "grx.h states the size of the fixed scratch array");
 
 // Bitmap of vertices with at least one edge (int32 offsets).
 __global__ void k_noalloc_nz(const int32_t *ro, int32_t nv, uint32_t *bits, int64_t words) {
@@ -100,6 +101,12 @@ extern "C" grx_status bfs_noalloc(int64_t nv, int64_t ne, const int32_t *row_off
     grx_opts o;
     grx_resolve_opts(opts, &o);
     if (o.collect_stats) return grx_fail(GRX_EINVAL, "bfs_noalloc: collect_stats is not supported");
+    // The CUDA-graph level loop instantiates a graph and keeps its arguments
+    // in device memory of their own: both would be allocations.
+    if (o.loop == GRX_LOOP_GRAPH)
+        return grx_fail(GRX_EINVAL, "bfs_noalloc: GRX_LOOP_GRAPH allocates; use the persistent or host loop");
+    if (o.loop != GRX_LOOP_PERSISTENT && o.loop != GRX_LOOP_HOST)
+        return grx_fail(GRX_EINVAL, "bfs_noalloc: bad loop %d", o.loop);
     if (o.direction < GRX_DIR_AUTO || o.direction > GRX_DIR_PULL)
         return grx_fail(GRX_EINVAL, "bfs_noalloc: bad direction %d", o.direction);
     int dev = 0;
@@ -141,8 +148,6 @@ extern "C" grx_status bfs_noalloc(int64_t nv, int64_t ne, const int32_t *row_off
         g.qe[i] = sc->qe[i];
         g.qr[i] = sc->qr[i];
     }
-    g.ulist[0] = sc->ulist[0];
-    g.ulist[1] = sc->ulist[1];
     g.ctl = &sc->ctl;
     g.bar_flags = sc->bar_flags;
     g.ws_ready = 1;

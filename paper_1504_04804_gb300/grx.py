@@ -363,6 +363,26 @@ def pagerank_block(g: Graph, shift: int):
 
 
 GRX_NOALLOC_MAX_NV = 1 << 19
+GRX_NOALLOC_SCRATCH_BYTES = 19219328
+
+
+def _noalloc_tensor(name: str, t, numel: int | None = None):
+    """Argument checks of bfs_noalloc: an int32, contiguous CUDA tensor on the
+    current device (the library reads it as a raw device pointer, and its
+    scratch array is the current device's)."""
+    if not isinstance(t, torch.Tensor):
+        raise ValueError(f"bfs_noalloc: {name} must be a torch.Tensor")
+    if t.dtype != torch.int32:
+        raise ValueError(f"bfs_noalloc: {name} must be int32 (got {t.dtype})")
+    if not t.is_cuda:
+        raise ValueError(f"bfs_noalloc: {name} must be a CUDA tensor")
+    if t.device.index != torch.cuda.current_device():
+        raise ValueError(f"bfs_noalloc: {name} is on cuda:{t.device.index}, the current device is "
+                         f"cuda:{torch.cuda.current_device()}")
+    if not t.is_contiguous():
+        raise ValueError(f"bfs_noalloc: {name} must be contiguous")
+    if numel is not None and t.numel() != numel:
+        raise ValueError(f"bfs_noalloc: {name} must have {numel} elements (got {t.numel()})")
 
 
 def bfs_noalloc(row_offsets: torch.Tensor, col_indices: torch.Tensor, src: int, depth_out=None,
@@ -371,8 +391,17 @@ def bfs_noalloc(row_offsets: torch.Tensor, col_indices: torch.Tensor, src: int, 
     device allocation by the library: for callers that cannot allocate.  The
     output tensors, if not given, are created here by torch (the library
     itself allocates nothing).  Limited to GRX_NOALLOC_MAX_NV vertices; calls
-    share one fixed scratch array, so calls overlapping on the GPU race."""
+    share one fixed scratch array, so calls overlapping on the GPU race.
+    Every tensor must be int32, contiguous and on the current CUDA device
+    (ValueError otherwise)."""
+    _noalloc_tensor("row_offsets", row_offsets)
+    _noalloc_tensor("col_indices", col_indices)
     nv = row_offsets.numel() - 1
+    for name, t in (("depth_out", depth_out), ("parent_out", parent_out)):
+        if t is not None:
+            _noalloc_tensor(name, t, nv)
+    if status_out is not None:
+        _noalloc_tensor("status_out", status_out, 1)
     dev = row_offsets.device.index
     d = _out(depth_out, nv, torch.int32, dev)
     _check(lib().bfs_noalloc(nv, col_indices.numel(), row_offsets.data_ptr(),

@@ -73,3 +73,35 @@ def test_argument_errors_without_gpu():
     out = ctypes.c_void_p()
     assert lib.graph_load_csr(None, 4, 0, None, 0, None, None, 0, None, ctypes.byref(out)) == grx.GRX_EINVAL
     assert lib.grx_rmat_edges(0, 10, 1, 0, 0, 0, None, None, None) == grx.GRX_EINVAL
+
+
+def test_noalloc_argument_checks_without_gpu():
+    """bfs_noalloc refuses the CUDA-graph loop (it would allocate) before any
+    CUDA call, and its binding refuses tensors the library cannot read."""
+    import torch
+    lib = grx.lib()
+    o = grx.opts(loop=grx.GRX_LOOP_GRAPH)
+    # the pointers are never dereferenced: the option check comes first
+    rc = lib.bfs_noalloc(16, 0, 16, None, 0, 16, None, None, ctypes.byref(o), None)
+    assert rc == grx.GRX_EINVAL
+    assert b"GRX_LOOP_GRAPH" in lib.grx_last_error()
+    o = grx.opts(loop=7)
+    assert lib.bfs_noalloc(16, 0, 16, None, 0, 16, None, None, ctypes.byref(o), None) == grx.GRX_EINVAL
+    ro = torch.zeros(17, dtype=torch.int32)
+    col = torch.zeros(0, dtype=torch.int32)
+    with pytest.raises(ValueError, match="int32"):
+        grx.bfs_noalloc(ro.to(torch.int64), col, 0)
+    with pytest.raises(ValueError, match="CUDA"):
+        grx.bfs_noalloc(ro, col, 0)
+    with pytest.raises(ValueError, match="Tensor"):
+        grx.bfs_noalloc([0] * 17, col, 0)
+    assert grx.GRX_NOALLOC_SCRATCH_BYTES == _header_define("GRX_NOALLOC_SCRATCH_BYTES")
+    assert grx.GRX_NOALLOC_MAX_NV == eval(_header_define("GRX_NOALLOC_MAX_NV", raw=True))
+
+
+def _header_define(name, raw=False):
+    for h in HEADERS:
+        m = re.search(rf"^#define {name} (.+)$", open(h).read(), flags=re.M)
+        if m:
+            return m.group(1).strip() if raw else int(m.group(1))
+    raise KeyError(name)

@@ -4,7 +4,8 @@ offsets exactly as the benchmark's default workload, with the library's
 launch configuration.  Every primitive is compared with the CPU oracle on
 seeded sources of the benchmark's own source list: BFS depths, SSSP
 distances and CC labels bit-exact, PageRank within 1e-5 relative, BC within
-1e-9 relative, and two lanes of a 64-lane multi-source BFS."""
+1e-9 relative, and two lanes of a 64-lane multi-source BFS.  R-MAT 24 and 26
+check PageRank's 20-iteration result at every vertex."""
 import os
 
 import numpy as np
@@ -126,42 +127,68 @@ def check_lanes_parallel(ro, col, lanes, row_of, chunk=16):
     return counts
 
 
-def test_rmat26_dobfs_multi_source_and_pagerank_step():
+def _pr_max_rel_err(got, want):
+    got = np.asarray(got, dtype=np.float64)
+    rel = np.abs(got - want) / want
+    v = int(np.argmax(rel))
+    return float(rel[v]), v
+
+
+def test_pagerank_rmat24_twenty_iterations():
+    """R-MAT scale 24 (16.8M vertices, ~520M directed edges): the FP32 ranks
+    after 20 iterations against the oracle's FP64 20-iteration result at every
+    vertex, max relative error <= 1e-5 (hubs here sum over a million terms)."""
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    build.build()
+    from paper_1504_04804_gb300 import grx
+    ro, col, _ = grx.rmat_graph_device(24, 16, seed=24)
+    g = grx.graph_load_csr(ro, col, None)
+    roh, colh = ro.cpu().numpy().astype(np.int64), col.cpu().numpy()
+    got = grx.pagerank(g, 0.85, 20).cpu().numpy()
+    grx.graph_status(g)
+    want = oracle.pagerank(roh, colh, 0.85, 20)
+    err, v = _pr_max_rel_err(got, want)
+    assert err <= 1e-5, f"max relative error {err:.3e} at vertex {v} (degree {roh[v + 1] - roh[v]})"
+    print(f"pagerank R-MAT 24: max relative error {err:.3e} at vertex {v}")
+
+
+def test_rmat26_dobfs_multi_source_and_pagerank():
     """R-MAT scale 26 with int64 offsets, as the benchmark loads it: one
     DOBFS source and two of the 64 multi-source lanes bit-exact against the
     oracle, every lane against the BFS invariants on host threads, and nine
-    lanes against single-source BFS on the GPU; PageRank:
-    the 20th iteration recomputed in float64 at 256 seeded vertices from the
-    GPU's 19th, within 1e-5, and the ranks summing to 1."""
+    lanes against single-source BFS on the GPU; PageRank after 20 iterations
+    against the oracle's FP64 20-iteration result at every vertex (max
+    relative error <= 1e-5; the oracle runs on a host thread meanwhile)."""
     if not torch.cuda.is_available():
         pytest.skip("no CUDA device")
     if torch.cuda.mem_get_info()[0] < 60e9:
         pytest.skip("needs 60 GB of free device memory")
     build.build()
+    from concurrent.futures import ThreadPoolExecutor
     from paper_1504_04804_gb300 import grx
     ro, col, _ = grx.rmat_graph_device(26, 16, seed=26)
     g = grx.graph_load_csr(ro, col, None, offsets64=True)
     roh, colh = ro.cpu().numpy().astype(np.int64), col.cpu().numpy()
-    src = int(inputs.pick_sources(roh, 16, 1)[0])
-    assert np.array_equal(grx.bfs(g, src).cpu().numpy(), oracle.bfs(roh, colh, src))
-    lanes = [int(x) for x in inputs.pick_sources(roh, 64, 5)]
-    d = grx.bfs_multi(g, lanes)
-    for b in (0, 63):
-        assert np.array_equal(d[b].cpu().numpy(), oracle.bfs(roh, colh, lanes[b])), b
-    for b in range(1, 63, 7):
-        assert torch.equal(d[b], grx.bfs(g, lanes[b])), b
-    # every lane against the BFS invariants (multithreaded host checker)
-    assert check_lanes_parallel(roh, colh, lanes, lambda b: d[b].cpu().numpy()) == [0] * 64
-    del d
-    r19 = grx.pagerank(g, 0.85, 19).cpu().numpy().astype(np.float64)
-    r20 = grx.pagerank(g, 0.85, 20).cpu().numpy().astype(np.float64)
-    assert abs(r20.sum() - 1.0) < 1e-3
-    nv = roh.shape[0] - 1
-    deg = np.diff(roh)
-    dangling = r19[deg == 0].sum()
-    rng = np.random.default_rng(26)
-    for v in rng.choice(np.flatnonzero(deg > 0), size=256, replace=False):
-        nb = colh[roh[v]:roh[v + 1]]
-        want = (1 - 0.85) / nv + 0.85 * (np.sum(r19[nb] / deg[nb]) + dangling / nv)
-        assert abs(r20[v] - want) <= 1e-5 * want, int(v)
-    grx.graph_status(g)
+    pool = ThreadPoolExecutor(max_workers=1)
+    pr_want = pool.submit(oracle.pagerank, roh, colh, 0.85, 20)   # ~minutes of one core
+    try:
+        src = int(inputs.pick_sources(roh, 16, 1)[0])
+        assert np.array_equal(grx.bfs(g, src).cpu().numpy(), oracle.bfs(roh, colh, src))
+        lanes = [int(x) for x in inputs.pick_sources(roh, 64, 5)]
+        d = grx.bfs_multi(g, lanes)
+        for b in (0, 63):
+            assert np.array_equal(d[b].cpu().numpy(), oracle.bfs(roh, colh, lanes[b])), b
+        for b in range(1, 63, 7):
+            assert torch.equal(d[b], grx.bfs(g, lanes[b])), b
+        # every lane against the BFS invariants (multithreaded host checker)
+        assert check_lanes_parallel(roh, colh, lanes, lambda b: d[b].cpu().numpy()) == [0] * 64
+        del d
+        r20 = grx.pagerank(g, 0.85, 20).cpu().numpy()
+        grx.graph_status(g)
+        assert abs(r20.astype(np.float64).sum() - 1.0) < 1e-3
+        err, v = _pr_max_rel_err(r20, pr_want.result())
+        assert err <= 1e-5, f"max relative error {err:.3e} at vertex {v} (degree {roh[v + 1] - roh[v]})"
+        print(f"pagerank R-MAT 26: max relative error {err:.3e} at vertex {v}")
+    finally:
+        pool.shutdown(wait=True)
