@@ -259,7 +259,7 @@ grx_status grx_pagerank_block(grx_graph *g, int shift);
  *   status_out   int32[1] or NULL: receives the device-side status of this
  *                call (0, or GRX_ETIMEOUT if a bounded wait ran out)
  * All traversal scratch lives in one fixed __device__ array sized for
- * GRX_NOALLOC_MAX_NV vertices (GRX_NOALLOC_SCRATCH_BYTES, about 19.2 MB),
+ * GRX_NOALLOC_MAX_NV vertices (GRX_NOALLOC_SCRATCH_BYTES, about 23.4 MB),
  * which every GPU that loads the library holds until the process exits.  nv
  * above that limit returns GRX_ERANGE; ne must be below 2^31.  opts as for
  * bfs, except that collect_stats must be 0 and loop must be
@@ -270,7 +270,7 @@ grx_status grx_pagerank_block(grx_graph *g, int shift);
  * stream capture.  Every call shares the array and clears what it needs;
  * calls whose GPU work overlaps race on it, so order them (one stream). */
 #define GRX_NOALLOC_MAX_NV (1 << 19)
-#define GRX_NOALLOC_SCRATCH_BYTES 19219328
+#define GRX_NOALLOC_SCRATCH_BYTES 23413632
 grx_status bfs_noalloc(int64_t nv, int64_t ne, const int32_t *row_offsets,
                        const int32_t *col_indices, int32_t src, int32_t *depth_out,
                        int32_t *parent_out, int32_t *status_out, const grx_opts *opts,

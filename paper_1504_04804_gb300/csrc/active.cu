@@ -150,3 +150,33 @@ grx_status grx_build_active(grx_graph *g, cudaStream_t s) {
     if (e != cudaSuccess) return grx_cuda_fail(e, "active list: fill");
     return GRX_OK;
 }
+
+// ---------------------------------------------------------------------------
+// First two neighbours of every row, side by side: the probe a pull step makes
+// first for each candidate (its first neighbours in row order) becomes one
+// coalesced 8-byte load per candidate instead of a row-offset load followed by
+// a scattered column load.  -1 marks a missing neighbour.
+// ---------------------------------------------------------------------------
+namespace {
+
+template <typename OffT>
+__global__ void k_first2(const OffT *ro, const int32_t *col, int64_t nv, int2 *first2) {
+    for (int64_t v = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; v < nv;
+         v += (int64_t)gridDim.x * blockDim.x) {
+        const OffT b = ro[v], e = ro[v + 1];
+        first2[v] = make_int2(e > b ? col[b] : -1, e > b + 1 ? col[b + 1] : -1);
+    }
+}
+
+}  // namespace
+
+grx_status grx_build_first2(grx_graph *g, cudaStream_t s) {
+    const int64_t nv = g->nv;
+    const int blocks = (int)((nv + 255) / 256 < 65536 ? (nv + 255) / 256 : 65536);
+    if (g->off64)
+        k_first2<int64_t><<<blocks, 256, 0, s>>>((const int64_t *)g->ro, g->col, nv, g->first2);
+    else
+        k_first2<int32_t><<<blocks, 256, 0, s>>>((const int32_t *)g->ro, g->col, nv, g->first2);
+    GRX_CUDA(cudaGetLastError());
+    return GRX_OK;
+}

@@ -64,17 +64,11 @@ constexpr int BFS_BLOCK = 256;
 constexpr int WARPS = BFS_BLOCK / 32;
 constexpr int PUSH_ITEMS = GRX_PUSH_ITEMS;
 constexpr int WTILE = 32 * PUSH_ITEMS;              // edges per warp tile
-#ifndef GRX_PULL_LIGHT
-#define GRX_PULL_LIGHT 2
-#endif
-constexpr int PULL_LIGHT = GRX_PULL_LIGHT;          // neighbours probed per vertex first (1 or 2)
+constexpr int PULL_LIGHT = 2;                       // neighbours probed per vertex first
 #ifndef GRX_PULL_PER_LANE
 #define GRX_PULL_PER_LANE 4
 #endif
 constexpr int PULL_PER_LANE = GRX_PULL_PER_LANE;    // candidates per lane per round
-#ifndef GRX_PULL_PREFETCH
-#define GRX_PULL_PREFETCH 0                         // 1: next round's row offsets requested early (spills; slower at R-MAT 26)
-#endif
 constexpr int PULL_WCH = 32 * PULL_PER_LANE;        // candidates per warp round
 constexpr int PULL_HITEMS = PUSH_ITEMS;             // heavy-phase edges per lane per step
 constexpr int PULL_HSTEP = 32 * PULL_HITEMS;        // heavy-phase edges per warp step
@@ -82,7 +76,7 @@ constexpr int SC_VERTS = 32 * 32;                   // vertices of a 32-word chu
 static_assert(WTILE == 256 && PULL_HSTEP == 256, "warp_tile_rows8 covers 256-position tiles");
 
 enum { DIR_PUSH = 0, DIR_PULL = 1 };
-enum { OP_QPUSH, OP_BMARK, OP_BFINAL, OP_COMPACT, OP_PULL };
+enum { OP_QPUSH, OP_BMARK, OP_BFINAL, OP_COMPACT, OP_PULL, OP_PULL_LIST };
 
 struct LevelState {
     int L;              // level being expanded (frontier = vertices at depth L)
@@ -98,6 +92,11 @@ struct LevelState {
     uint8_t bmp;        // push by bitmap marking + finalize phase
     uint8_t compact;    // push whose frontier is first compacted F_L -> Q_L
     uint8_t phase;      // phase of the level being run
+    uint8_t uin;        // U_L (candidates left unfound by a pull level L-1) exists
+    uint8_t lmode;      // pull over the list U_L instead of a sweep of all chunks
+    uint8_t uwrite;     // this pull level writes U_{L+1}
+    uint32_t seq;       // phases run so far in this traversal (chunk-counter ring index)
+    uint32_t ucnt;      // |U_L|
     uint32_t q, T;      // |Q_L| and its edge count
     uint32_t nprev;     // |Q_{L-1}|
     unsigned long long vcount;   // visited vertices including Q_L
@@ -124,7 +123,10 @@ struct BfsArgs {
     int mode;
     int exact_fv;
     float alpha, beta;
+    int32_t *U[2];                // candidate lists left by pull levels, ping-pong by level
+    const int2 *first2;           // first two neighbours of each row, or NULL (read the CSR)
     uint32_t bmp_min_T;           // push levels with at least this many edges mark a bitmap
+    uint32_t ulist_max;           // a pull level works on U_L when |U_L| <= ulist_max
     unsigned long long timeout_ns;
     int32_t src;
 };
@@ -159,7 +161,7 @@ __device__ __forceinline__ int level_phases(const LevelState &s) {
 }
 
 __device__ __forceinline__ int level_op(const LevelState &s) {
-    if (s.dir == DIR_PULL) return OP_PULL;
+    if (s.dir == DIR_PULL) return s.lmode ? OP_PULL_LIST : OP_PULL;
     const int p = (int)s.phase - (int)s.compact;
     if (p < 0) return OP_COMPACT;
     if (p == 0) return s.bmp ? OP_BMARK : OP_QPUSH;
@@ -170,6 +172,8 @@ template <typename OffT>
 __device__ __forceinline__ void set_kind(const BfsArgs<OffT> &a, LevelState &s) {
     s.compact = s.dir == DIR_PUSH && !s.qin;
     s.bmp = s.dir == DIR_PUSH && s.T >= a.bmp_min_T;
+    s.lmode = s.dir == DIR_PULL && s.uin && s.ucnt <= a.ulist_max;
+    s.uwrite = s.dir == DIR_PULL;
     // a queue push feeds F_{L+1} only while a pull may still follow
     s.fwrite = s.dir == DIR_PULL || s.bmp || (a.mode == GRX_DIR_AUTO && !s.back);
 }
@@ -197,6 +201,7 @@ __device__ LevelState initial_state(const BfsArgs<OffT> &a) {
 template <typename OffT>
 __device__ LevelState next_state(const BfsArgs<OffT> &a, const LevelState &st, bool stats) {
     LevelState ns = st;
+    ns.seq = st.seq + 1;
     if ((int)st.phase + 1 < level_phases(st)) {
         ns.phase = st.phase + 1;
         return ns;
@@ -211,7 +216,9 @@ __device__ LevelState next_state(const BfsArgs<OffT> &a, const LevelState &st, b
     ns.fclear = st.fprev;
     ns.fprev = st.fwrite;
     ns.qprev_ok = st.qin || st.compact;
-    ns.qin = st.dir == DIR_PUSH;
+    ns.qin = st.dir == DIR_PUSH || st.lmode;     // a list pull appends what it finds
+    ns.uin = st.uwrite;
+    ns.ucnt = st.uwrite ? ld_relaxed_u32(&a.ctl->ucount[(st.L + 1) & 3]) : 0u;
     if (stats && blockIdx.x == 0 && st.L < GRX_MAX_LEVELS_STATS) a.stats->discovered[st.L] = ns.q;
     if (ns.q == 0) {
         ns.done = 1;
@@ -292,6 +299,15 @@ __device__ __forceinline__ int64_t push_tile(const BfsArgs<OffT> &a, const int32
     __syncwarp();
     // the element holding e1 starts the next tile
     return (next_start == e1) ? i0 + n : i0 + n - 1;
+}
+
+// Next 32-word chunk of a word-owning sweep for the calling warp: chunks are
+// handed out in increasing order from the phase's counter, so warps that
+// meet cheap chunks take more of them and all finish together.
+__device__ __forceinline__ int64_t grab_chunk(unsigned int *ctr) {
+    unsigned int c = 0;
+    if ((threadIdx.x & 31) == 0) c = atomicAdd(ctr, 1u);
+    return (int64_t)__shfl_sync(GRX_FULL_MASK, c, 0);
 }
 
 // Lanes aiming at the same vertex: only the lowest one keeps its bit.
@@ -444,8 +460,16 @@ __device__ void bitmap_to_queue(const BfsArgs<OffT> &a, const LevelState &st, Pu
     unsigned long long *ctr = FINAL ? &a.ctl->qpack[(L + 1) & 3] : &a.ctl->cpack;
     const unsigned int lane = threadIdx.x & 31;
     const int64_t nsc = (a.words + 31) / 32;
-    const int64_t nwarps = (int64_t)gridDim.x * WARPS;
-    for (int64_t sc = (int64_t)blockIdx.x * WARPS + (threadIdx.x >> 5); sc < nsc; sc += nwarps) {
+    unsigned int *wq = &a.ctl->wq[st.seq & 3];
+    // first chunk: the warp's own index; later ones from the phase's counter
+    // (offset by the warp count).  The next chunk is requested at the start
+    // of the body and read at its end, so the counter's round trip overlaps
+    // this chunk's work.
+    const unsigned int nwarps = gridDim.x * WARPS;
+    int64_t sc = (int64_t)blockIdx.x * WARPS + (threadIdx.x >> 5);
+    while (sc < nsc) {
+        unsigned int nn = 0;
+        if (lane == 0) nn = nwarps + atomicAdd(wq, 1u);
         const int64_t wd = sc * 32 + lane;
         const uint32_t bits = wd < a.words ? __ldcg(B + wd) : 0u;
         if (FINAL && bits) {
@@ -481,22 +505,187 @@ __device__ void bitmap_to_queue(const BfsArgs<OffT> &a, const LevelState &st, Pu
             warp_append_items<PULL_PER_LANE, OffT>(v, deg, rb, app, Qv, Qe, Qr, ctr);
         }
         __syncwarp();
+        sc = (int64_t)__shfl_sync(GRX_FULL_MASK, nn, 0);
     }
 }
 
-// Pull level: the owner of each 32-word chunk finds a frontier parent for the
-// chunk's unvisited non-isolated vertices and writes the chunk's visited and
-// F_{L+1} words (and, with fclear, zeroes its F_{L-1} words).
-//  1. candidates of the chunk, PULL_WCH per round (PULL_PER_LANE per lane);
-//  2. light phase: the first PULL_LIGHT neighbours of every candidate, all in
+// Row start, degree and first two neighbours of the candidates a lane takes
+// in the round starting at list entry `base` (entries base + k*32 + lane;
+// vertex = origin + list[i]); the three loads of a candidate are independent.
+template <typename OffT>
+__device__ __forceinline__ void load_candidates(const BfsArgs<OffT> &a, int64_t origin, const uint16_t *list,
+                                                int base, int n, int32_t (&v)[PULL_PER_LANE],
+                                                OffT (&b)[PULL_PER_LANE], uint32_t (&deg)[PULL_PER_LANE],
+                                                int2 (&f2)[PULL_PER_LANE]) {
+    const unsigned int lane = threadIdx.x & 31;
+#pragma unroll
+    for (int k = 0; k < PULL_PER_LANE; ++k) {
+        const int i = base + k * 32 + (int)lane;
+        v[k] = i < n ? (int32_t)(origin + list[i]) : -1;
+        OffT e = 0;
+        b[k] = 0;
+        f2[k] = make_int2(-1, -1);
+        if (v[k] >= 0) {
+            b[k] = __ldg(a.ro + v[k]);
+            e = __ldg(a.ro + v[k] + 1);
+            if (a.first2) f2[k] = __ldg(a.first2 + v[k]);
+        }
+        deg[k] = (uint32_t)(e - b[k]);
+    }
+}
+
+// One pull round over up to PULL_WCH candidates of a warp (lane holds
+// candidates k*32 + lane): v (-1 = empty slot), row start b, degree deg.
+//  light phase: the first PULL_LIGHT neighbours of every candidate, all in
 //     flight at once;
-//  3. heavy phase: the round's lists without a hit yet are concatenated and
-//     consumed front to back in load-balanced steps of PULL_HSTEP edges
-//     shared by the whole warp; a list leaves once any of its edges hits the
-//     frontier (any frontier neighbour is a valid parent);
-//  4. found vertices are labelled; their bits collect in the chunk's masks.
-// F_L is read-only during the level, so its probes may be served by L1 (hot
-// words of high-degree vertices are then not refetched from L2 by every warp).
+//  heavy phase: the lists without a hit yet are concatenated and consumed
+//     front to back in load-balanced steps of PULL_HSTEP edges shared by the
+//     whole warp; a list leaves once any of its edges hits the frontier (any
+//     frontier neighbour is a valid parent: edge skipping).
+// Returns in par[k] the parent found (-1: none).  F_L is read-only during the
+// level, so its probes may be served by L1 (hot words of high-degree vertices
+// are then not refetched from L2 by every warp).
+template <typename OffT, bool STATS>
+__device__ __forceinline__ void pull_round(const BfsArgs<OffT> &a, const uint32_t *Fin,
+                                           PullWarpSmem<OffT> &w, const int32_t (&v)[PULL_PER_LANE],
+                                           const OffT (&b)[PULL_PER_LANE],
+                                           const uint32_t (&deg)[PULL_PER_LANE],
+                                           const int2 (&f2)[PULL_PER_LANE],
+                                           int32_t (&par)[PULL_PER_LANE],
+                                           unsigned long long &scanned_e, unsigned long long &scanned_v) {
+    const unsigned int lane = threadIdx.x & 31;
+    static_assert(PULL_LIGHT == 2, "the light phase probes the two neighbours of first2");
+    int32_t u0[PULL_PER_LANE], u1[PULL_PER_LANE];
+#pragma unroll
+    for (int k = 0; k < PULL_PER_LANE; ++k) {
+        if (a.first2) {          // loaded by the caller beside the row offsets
+            u0[k] = f2[k].x;
+            u1[k] = f2[k].y;
+        } else {
+            u0[k] = deg[k] > 0 ? __ldg(a.col + b[k]) : -1;
+            u1[k] = deg[k] > 1 ? __ldg(a.col + b[k] + 1) : -1;
+        }
+    }
+    uint32_t f0[PULL_PER_LANE], f1[PULL_PER_LANE];
+#pragma unroll
+    for (int k = 0; k < PULL_PER_LANE; ++k) {
+        f0[k] = u0[k] >= 0 ? __ldca(Fin + (u0[k] >> 5)) : 0u;
+        f1[k] = u1[k] >= 0 ? __ldca(Fin + (u1[k] >> 5)) : 0u;
+    }
+    uint32_t heavy = 0;
+#pragma unroll
+    for (int k = 0; k < PULL_PER_LANE; ++k) {
+        par[k] = -1;
+        if (u0[k] >= 0 && ((f0[k] >> (u0[k] & 31)) & 1u)) par[k] = u0[k];
+        else if (u1[k] >= 0 && ((f1[k] >> (u1[k] & 31)) & 1u)) par[k] = u1[k];
+        if (STATS && v[k] >= 0) {
+            scanned_v += 1;
+            scanned_e += (unsigned long long)min((uint32_t)PULL_LIGHT, deg[k]);
+        }
+        if (v[k] >= 0 && par[k] < 0 && deg[k] > PULL_LIGHT) heavy |= 1u << k;
+    }
+    int nh = 0;
+    int hpos[PULL_PER_LANE];
+#pragma unroll
+    for (int k = 0; k < PULL_PER_LANE; ++k) {
+        const unsigned int m = __ballot_sync(GRX_FULL_MASK, heavy >> k & 1u);
+        hpos[k] = nh + __popc(m & lanemask_lt());
+        if (heavy >> k & 1u) {
+            w.hb[hpos[k]] = b[k] + PULL_LIGHT;
+            w.hl[hpos[k]] = deg[k] - PULL_LIGHT;
+            w.hpar[hpos[k]] = -1;
+        }
+        nh += __popc(m);
+    }
+    __syncwarp();
+    while (nh > 0) {
+        // exclusive prefix of the unresolved lengths; lane owns entries lane*PULL_PER_LANE + r
+        uint32_t ln[PULL_PER_LANE], lsum = 0;
+#pragma unroll
+        for (int r = 0; r < PULL_PER_LANE; ++r) {
+            const int h = (int)lane * PULL_PER_LANE + r;
+            ln[r] = (h < nh && w.hpar[h] < 0) ? w.hl[h] : 0u;
+            lsum += ln[r];
+        }
+        uint32_t x = lsum;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const uint32_t y = __shfl_up_sync(GRX_FULL_MASK, x, o);
+            if (lane >= (unsigned)o) x += y;
+        }
+        const uint32_t total = __shfl_sync(GRX_FULL_MASK, x, 31);
+        if (total == 0) break;
+        uint32_t off = x - lsum;
+#pragma unroll
+        for (int r = 0; r < PULL_PER_LANE; ++r) {
+            const int h = (int)lane * PULL_PER_LANE + r;
+            if (h < nh) w.hofs[h] = off;
+            off += ln[r];
+        }
+        if (lane == 0) w.hofs[nh] = total;
+        __syncwarp();
+        const uint32_t steplen = min(total, (uint32_t)PULL_HSTEP);
+        int hrow[PULL_HITEMS];
+        warp_tile_rows8(w.hrid, w.hofs, 0u, nh, hrow);
+        const uint32_t j0 = lane * PULL_HITEMS;
+        int32_t uu[PULL_HITEMS];
+#pragma unroll
+        for (int k = 0; k < PULL_HITEMS; ++k) {
+            const uint32_t j = j0 + k;
+            const int h = hrow[k];
+            uu[k] = j < steplen ? __ldg(a.col + w.hb[h] + (OffT)(j - w.hofs[h])) : -1;
+        }
+#pragma unroll
+        for (int k = 0; k < PULL_HITEMS; ++k) {
+            if (uu[k] >= 0 && ((__ldca(Fin + (uu[k] >> 5)) >> (uu[k] & 31)) & 1u))
+                w.hpar[hrow[k]] = uu[k];          // any hit is a valid parent
+        }
+        if (STATS && j0 < steplen)
+            scanned_e += (unsigned long long)min((uint32_t)PULL_HITEMS, steplen - j0);
+        __syncwarp();
+        // the step consumed the first steplen edges of the concatenation
+#pragma unroll
+        for (int r = 0; r < PULL_PER_LANE; ++r) {
+            const int h = (int)lane * PULL_PER_LANE + r;
+            if (ln[r] > 0 && w.hpar[h] < 0) {
+                const uint32_t o = w.hofs[h];
+                const uint32_t used = steplen > o ? min(ln[r], steplen - o) : 0u;
+                w.hb[h] += (OffT)used;
+                w.hl[h] = ln[r] - used;
+            }
+        }
+        __syncwarp();
+    }
+#pragma unroll
+    for (int k = 0; k < PULL_PER_LANE; ++k)
+        if (heavy >> k & 1u) par[k] = w.hpar[hpos[k]];
+    __syncwarp();
+}
+
+// Appends the vertices of bit set `bits` (lane holds word wd = word index of
+// its 32 vertices) to list[] with one counter update per warp; order within
+// the warp's batch is the vertex order.  Uses w.list as staging.
+template <typename OffT>
+__device__ __forceinline__ void warp_append_bits(uint32_t bits, int64_t sc, PullWarpSmem<OffT> &w,
+                                                 int32_t *list, unsigned int *ctr) {
+    const unsigned int lane = threadIdx.x & 31;
+    const int n = warp_compact_bits(bits, w.list);
+    if (n == 0) return;
+    unsigned int base = 0;
+    if (lane == 0) base = atomicAdd(ctr, (unsigned)n);
+    base = __shfl_sync(GRX_FULL_MASK, base, 0);
+    for (int i = (int)lane; i < n; i += 32) list[base + i] = (int32_t)(sc * SC_VERTS + w.list[i]);
+    __syncwarp();
+}
+
+// Pull level over all vertices (sweep): the owner of each 32-word chunk finds
+// a frontier parent for the chunk's unvisited non-isolated vertices and
+// writes the chunk's visited and F_{L+1} words (and, with fclear, zeroes its
+// F_{L-1} words).  Chunks come from the phase's counter.  Candidates are
+// compacted in shared memory and probed PULL_WCH per round (pull_round); the
+// found vertices are labelled and their bits collect in the chunk's masks.
+// The candidates left unfound form the list U_{L+1} (in chunk order), which a
+// following pull level may work on instead of sweeping again.
 template <typename OffT, bool PARENT, bool STATS>
 __device__ void pull_level(const BfsArgs<OffT> &a, const LevelState &st, PullWarpSmem<OffT> &w,
                            unsigned long long &scanned_e, unsigned long long &scanned_v) {
@@ -505,11 +694,21 @@ __device__ void pull_level(const BfsArgs<OffT> &a, const LevelState &st, PullWar
     const uint32_t *Fin = pick3(a.F[0], a.F[1], a.F[2], L % 3);
     uint32_t *Fout = pick3(a.F[0], a.F[1], a.F[2], (L + 1) % 3);
     uint32_t *Fold = pick3(a.F[0], a.F[1], a.F[2], (L + 2) % 3);
+    int32_t *Unext = a.U[(L + 1) & 1];
+    unsigned int *uctr = &a.ctl->ucount[(L + 1) & 3];
     const int64_t nsc = (a.words + 31) / 32;
-    const int64_t nwarps = (int64_t)gridDim.x * WARPS;
+    unsigned int *wq = &a.ctl->wq[st.seq & 3];
     uint32_t nfound = 0;
     uint32_t nedges = 0;
-    for (int64_t sc = (int64_t)blockIdx.x * WARPS + (threadIdx.x >> 5); sc < nsc; sc += nwarps) {
+    // first chunk: the warp's own index; later ones from the phase's counter
+    // (offset by the warp count).  The next chunk is requested at the start
+    // of the body and read at its end, so the counter's round trip overlaps
+    // this chunk's work.
+    const unsigned int nwarps = gridDim.x * WARPS;
+    int64_t sc = (int64_t)blockIdx.x * WARPS + (threadIdx.x >> 5);
+    while (sc < nsc) {
+        unsigned int nn = 0;
+        if (lane == 0) nn = nwarps + atomicAdd(wq, 1u);
         const int64_t wd = sc * 32 + lane;
         const bool own = wd < a.words;
         const uint32_t vis = own ? __ldcg(a.visited + wd) : 0xffffffffu;
@@ -517,149 +716,29 @@ __device__ void pull_level(const BfsArgs<OffT> &a, const LevelState &st, PullWar
         if (own && st.fclear) Fold[wd] = 0u;
         w.fb[lane] = 0u;
         const int n = warp_compact_bits(cand, w.list);
-        // 1. candidates: lane takes entries base + k*32 + lane; the next
-        // round's row offsets are requested before this round's probes
         int32_t vn[PULL_PER_LANE];
-        OffT bn[PULL_PER_LANE], en[PULL_PER_LANE];
-#pragma unroll
-        for (int k = 0; k < PULL_PER_LANE; ++k) {
-            const int i = k * 32 + (int)lane;
-            vn[k] = i < n ? (int32_t)(sc * SC_VERTS + w.list[i]) : -1;
-            bn[k] = vn[k] >= 0 ? __ldg(a.ro + vn[k]) : (OffT)0;
-            en[k] = vn[k] >= 0 ? __ldg(a.ro + vn[k] + 1) : (OffT)0;
-        }
+        OffT bn[PULL_PER_LANE];
+        uint32_t dn[PULL_PER_LANE];
+        int2 fn[PULL_PER_LANE];
+        load_candidates(a, sc * SC_VERTS, w.list, 0, n, vn, bn, dn, fn);
         for (int base = 0; base < n; base += PULL_WCH) {
             int32_t v[PULL_PER_LANE];
             OffT b[PULL_PER_LANE];
             uint32_t deg[PULL_PER_LANE];
+            int2 f2[PULL_PER_LANE];
 #pragma unroll
             for (int k = 0; k < PULL_PER_LANE; ++k) {
                 v[k] = vn[k];
                 b[k] = bn[k];
-                deg[k] = (uint32_t)(en[k] - bn[k]);
-            }
-#if GRX_PULL_PREFETCH
-#pragma unroll
-            for (int k = 0; k < PULL_PER_LANE; ++k) {
-                const int i = base + PULL_WCH + k * 32 + (int)lane;
-                vn[k] = i < n ? (int32_t)(sc * SC_VERTS + w.list[i]) : -1;
-                bn[k] = vn[k] >= 0 ? __ldg(a.ro + vn[k]) : (OffT)0;
-                en[k] = vn[k] >= 0 ? __ldg(a.ro + vn[k] + 1) : (OffT)0;
-            }
-#endif
-            // 2. light phase
-            static_assert(PULL_LIGHT == 1 || PULL_LIGHT == 2, "light phase probes 1 or 2 neighbours");
-            int32_t u0[PULL_PER_LANE], u1[PULL_PER_LANE];
-#pragma unroll
-            for (int k = 0; k < PULL_PER_LANE; ++k) {
-                u0[k] = deg[k] > 0 ? __ldg(a.col + b[k]) : -1;
-                u1[k] = (PULL_LIGHT > 1 && deg[k] > 1) ? __ldg(a.col + b[k] + 1) : -1;
-            }
-            uint32_t f0[PULL_PER_LANE], f1[PULL_PER_LANE];
-#pragma unroll
-            for (int k = 0; k < PULL_PER_LANE; ++k) {
-                f0[k] = u0[k] >= 0 ? __ldca(Fin + (u0[k] >> 5)) : 0u;
-                f1[k] = u1[k] >= 0 ? __ldca(Fin + (u1[k] >> 5)) : 0u;
+                deg[k] = dn[k];
+                f2[k] = fn[k];
             }
             int32_t par[PULL_PER_LANE];
-            uint32_t heavy = 0;
+            pull_round<OffT, STATS>(a, Fin, w, v, b, deg, f2, par, scanned_e, scanned_v);
+            load_candidates(a, sc * SC_VERTS, w.list, base + PULL_WCH, n, vn, bn, dn, fn);
+            // label the found vertices; their bits go to the chunk's word masks
 #pragma unroll
             for (int k = 0; k < PULL_PER_LANE; ++k) {
-                par[k] = -1;
-                if (u0[k] >= 0 && ((f0[k] >> (u0[k] & 31)) & 1u)) par[k] = u0[k];
-                else if (u1[k] >= 0 && ((f1[k] >> (u1[k] & 31)) & 1u)) par[k] = u1[k];
-                if (STATS && v[k] >= 0) {
-                    scanned_v += 1;
-                    scanned_e += (unsigned long long)min((uint32_t)PULL_LIGHT, deg[k]);
-                }
-                if (v[k] >= 0 && par[k] < 0 && deg[k] > PULL_LIGHT) heavy |= 1u << k;
-            }
-            // 3. heavy phase
-            int nh = 0;
-            int hpos[PULL_PER_LANE];
-#pragma unroll
-            for (int k = 0; k < PULL_PER_LANE; ++k) {
-                const unsigned int m = __ballot_sync(GRX_FULL_MASK, heavy >> k & 1u);
-                hpos[k] = nh + __popc(m & lanemask_lt());
-                if (heavy >> k & 1u) {
-                    w.hb[hpos[k]] = b[k] + PULL_LIGHT;
-                    w.hl[hpos[k]] = deg[k] - PULL_LIGHT;
-                    w.hpar[hpos[k]] = -1;
-                }
-                nh += __popc(m);
-            }
-            __syncwarp();
-            while (nh > 0) {
-                // exclusive prefix of the unresolved lengths; lane owns entries lane*PULL_PER_LANE + r
-                uint32_t ln[PULL_PER_LANE], lsum = 0;
-#pragma unroll
-                for (int r = 0; r < PULL_PER_LANE; ++r) {
-                    const int h = (int)lane * PULL_PER_LANE + r;
-                    ln[r] = (h < nh && w.hpar[h] < 0) ? w.hl[h] : 0u;
-                    lsum += ln[r];
-                }
-                uint32_t x = lsum;
-#pragma unroll
-                for (int o = 1; o < 32; o <<= 1) {
-                    const uint32_t y = __shfl_up_sync(GRX_FULL_MASK, x, o);
-                    if (lane >= (unsigned)o) x += y;
-                }
-                const uint32_t total = __shfl_sync(GRX_FULL_MASK, x, 31);
-                if (total == 0) break;
-                uint32_t off = x - lsum;
-#pragma unroll
-                for (int r = 0; r < PULL_PER_LANE; ++r) {
-                    const int h = (int)lane * PULL_PER_LANE + r;
-                    if (h < nh) w.hofs[h] = off;
-                    off += ln[r];
-                }
-                if (lane == 0) w.hofs[nh] = total;
-                __syncwarp();
-                const uint32_t steplen = min(total, (uint32_t)PULL_HSTEP);
-                int hrow[PULL_HITEMS];
-                warp_tile_rows8(w.hrid, w.hofs, 0u, nh, hrow);
-                const uint32_t j0 = lane * PULL_HITEMS;
-                int32_t uu[PULL_HITEMS];
-#pragma unroll
-                for (int k = 0; k < PULL_HITEMS; ++k) {
-                    const uint32_t j = j0 + k;
-                    const int h = hrow[k];
-                    uu[k] = j < steplen ? __ldg(a.col + w.hb[h] + (OffT)(j - w.hofs[h])) : -1;
-                }
-#pragma unroll
-                for (int k = 0; k < PULL_HITEMS; ++k) {
-                    if (uu[k] >= 0 && ((__ldca(Fin + (uu[k] >> 5)) >> (uu[k] & 31)) & 1u))
-                        w.hpar[hrow[k]] = uu[k];          // any hit is a valid parent
-                }
-                if (STATS && j0 < steplen)
-                    scanned_e += (unsigned long long)min((uint32_t)PULL_HITEMS, steplen - j0);
-                __syncwarp();
-                // the step consumed the first steplen edges of the concatenation
-#pragma unroll
-                for (int r = 0; r < PULL_PER_LANE; ++r) {
-                    const int h = (int)lane * PULL_PER_LANE + r;
-                    if (ln[r] > 0 && w.hpar[h] < 0) {
-                        const uint32_t o = w.hofs[h];
-                        const uint32_t used = steplen > o ? min(ln[r], steplen - o) : 0u;
-                        w.hb[h] += (OffT)used;
-                        w.hl[h] = ln[r] - used;
-                    }
-                }
-                __syncwarp();
-            }
-#if !GRX_PULL_PREFETCH
-#pragma unroll
-            for (int k = 0; k < PULL_PER_LANE; ++k) {
-                const int i = base + PULL_WCH + k * 32 + (int)lane;
-                vn[k] = i < n ? (int32_t)(sc * SC_VERTS + w.list[i]) : -1;
-                bn[k] = vn[k] >= 0 ? __ldg(a.ro + vn[k]) : (OffT)0;
-                en[k] = vn[k] >= 0 ? __ldg(a.ro + vn[k] + 1) : (OffT)0;
-            }
-#endif
-            // 4. label the found vertices; their bits go to the chunk's word masks
-#pragma unroll
-            for (int k = 0; k < PULL_PER_LANE; ++k) {
-                if (heavy >> k & 1u) par[k] = w.hpar[hpos[k]];
                 if (v[k] >= 0 && par[k] >= 0) {
                     a.depth[v[k]] = L + 1;
                     if (PARENT) a.parent[v[k]] = par[k];
@@ -670,17 +749,91 @@ __device__ void pull_level(const BfsArgs<OffT> &a, const LevelState &st, PullWar
             }
             __syncwarp();
         }
+        const uint32_t fb = w.fb[lane];
         if (own) {
-            const uint32_t fb = w.fb[lane];
             if (fb) a.visited[wd] = vis | fb;
             Fout[wd] = fb;               // whole word: F_{L+1} needs no clearing first
         }
         __syncwarp();
+        if (st.uwrite) warp_append_bits(cand & ~fb, sc, w, Unext, uctr);
+        sc = (int64_t)__shfl_sync(GRX_FULL_MASK, nn, 0);
     }
     // one counter update per warp: (found << 32 | their edges)
     const unsigned long long cnt = warp_sum((unsigned long long)nfound);
     const unsigned long long edg = warp_sum((unsigned long long)nedges);
     if (lane == 0 && cnt) atomicAdd(&a.ctl->qpack[(L + 1) & 3], (cnt << 32) | edg);
+}
+
+// Pull level over the list U_L of the candidates the previous pull level
+// left unfound (every one unvisited and non-isolated): slices of PULL_WCH
+// list entries per warp, one pull_round each.  Found vertices are labelled,
+// their bits set in visited and F_{L+1} (reductions: a word is shared with
+// other warps' vertices), and they are appended to Q_{L+1} with their degrees
+// and row starts, so a push level that follows needs no compaction.  The
+// unfound ones form U_{L+1}.
+template <typename OffT, bool PARENT, bool STATS>
+__device__ void pull_list(const BfsArgs<OffT> &a, const LevelState &st, PullWarpSmem<OffT> &w,
+                          unsigned long long &scanned_e, unsigned long long &scanned_v) {
+    const int L = st.L;
+    const unsigned int lane = threadIdx.x & 31;
+    const uint32_t *Fin = pick3(a.F[0], a.F[1], a.F[2], L % 3);
+    uint32_t *Fout = pick3(a.F[0], a.F[1], a.F[2], (L + 1) % 3);
+    int32_t *Qv_out = pick3(a.Q[0], a.Q[1], a.Q[2], (L + 1) % 3);
+    uint32_t *Qe_out = pick3(a.E[0], a.E[1], a.E[2], (L + 1) % 3);
+    OffT *Qr_out = pick3(a.R[0], a.R[1], a.R[2], (L + 1) % 3);
+    unsigned long long *qctr = &a.ctl->qpack[(L + 1) & 3];
+    const int32_t *U = a.U[L & 1];
+    int32_t *Unext = a.U[(L + 1) & 1];
+    unsigned int *uctr = &a.ctl->ucount[(L + 1) & 3];
+    const int64_t n = st.ucnt;
+    const int64_t nsl = (n + PULL_WCH - 1) / PULL_WCH;
+    unsigned int *wq = &a.ctl->wq[st.seq & 3];
+    const unsigned int nwarps = gridDim.x * WARPS;
+    int64_t sl = (int64_t)blockIdx.x * WARPS + (threadIdx.x >> 5);
+    for (; sl < nsl; sl = nwarps + grab_chunk(wq)) {
+        const int64_t base = sl * PULL_WCH;
+        int32_t v[PULL_PER_LANE];
+        OffT b[PULL_PER_LANE];
+        uint32_t deg[PULL_PER_LANE];
+        int2 f2[PULL_PER_LANE];
+#pragma unroll
+        for (int k = 0; k < PULL_PER_LANE; ++k) {
+            const int64_t i = base + k * 32 + (int)lane;
+            v[k] = i < n ? __ldcg(U + i) : -1;
+        }
+#pragma unroll
+        for (int k = 0; k < PULL_PER_LANE; ++k) {
+            OffT e = 0;
+            b[k] = 0;
+            f2[k] = make_int2(-1, -1);
+            if (v[k] >= 0) {
+                b[k] = __ldg(a.ro + v[k]);
+                e = __ldg(a.ro + v[k] + 1);
+                if (a.first2) f2[k] = __ldg(a.first2 + v[k]);
+            }
+            deg[k] = (uint32_t)(e - b[k]);
+        }
+        int32_t par[PULL_PER_LANE];
+        pull_round<OffT, STATS>(a, Fin, w, v, b, deg, f2, par, scanned_e, scanned_v);
+        uint32_t app = 0, left = 0;
+#pragma unroll
+        for (int k = 0; k < PULL_PER_LANE; ++k) {
+            if (v[k] < 0) continue;
+            if (par[k] >= 0) {
+                const uint32_t bit = 1u << (v[k] & 31);
+                a.depth[v[k]] = L + 1;
+                if (PARENT) a.parent[v[k]] = par[k];
+                atomicOr(a.visited + (v[k] >> 5), bit);
+                atomicOr(Fout + (v[k] >> 5), bit);
+                app |= 1u << k;
+            } else {
+                left |= 1u << k;
+            }
+        }
+        warp_append_items<PULL_PER_LANE, OffT>(v, deg, b, app, Qv_out, Qe_out, Qr_out, qctr);
+        if (st.uwrite) warp_append_list_items<PULL_PER_LANE>(v, left, Unext, uctr);
+        __syncwarp();
+    }
 }
 
 template <typename OffT, bool PARENT, bool STATS>
@@ -690,6 +843,9 @@ __device__ void run_phase(const BfsArgs<OffT> &a, const LevelState &st, WarpSmem
     if (blockIdx.x == 0 && threadIdx.x == 0) {
         // the compaction counter is only used by a first phase; zero it in a last one
         if ((int)st.phase + 1 == level_phases(st)) a.ctl->cpack = 0ull;
+        // chunk counter of the phase after next (phase seq + 2 runs after two barriers)
+        a.ctl->wq[(st.seq + 2) & 3] = 0u;
+        if (st.phase == 0) a.ctl->ucount[(L + 2) & 3] = 0u;
         if (st.phase == 0) {
             a.ctl->qpack[(L + 2) & 3] = 0ull;
             if (STATS && L < GRX_MAX_LEVELS_STATS) {
@@ -704,11 +860,13 @@ __device__ void run_phase(const BfsArgs<OffT> &a, const LevelState &st, WarpSmem
             }
         }
     }
-    if (st.phase == 0 && st.fclear && st.dir == DIR_PUSH) {
-        // zero F_{L-1} (pull levels do it in their word loop)
+    if (st.phase == 0 && st.fclear && (st.dir == DIR_PUSH || st.lmode)) {
+        // zero F_{L-1} (sweeping pull levels do it in their word loop)
         uint32_t *Fp = pick3(a.F[0], a.F[1], a.F[2], (L + 2) % 3);
-        if (st.qprev_ok) {
+        if (st.qprev_ok && (int64_t)st.nprev * 8 < a.words) {
             // F_{L-1} only holds bits of Q_{L-1}'s vertices: zero their words
+            // (scattered stores; a queue of more than words/8 entries costs
+            // more than zeroing every word with coalesced stores)
             const int32_t *Qp = pick3(a.Q[0], a.Q[1], a.Q[2], (L + 2) % 3);
             for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < (int64_t)st.nprev;
                  i += (int64_t)gridDim.x * blockDim.x)
@@ -726,7 +884,8 @@ __device__ void run_phase(const BfsArgs<OffT> &a, const LevelState &st, WarpSmem
     case OP_COMPACT: bitmap_to_queue<OffT, false>(a, st, w.l); break;
     default: {
         unsigned long long scanned_e = 0, scanned_v = 0;
-        pull_level<OffT, PARENT, STATS>(a, st, w.l, scanned_e, scanned_v);
+        if (op == OP_PULL_LIST) pull_list<OffT, PARENT, STATS>(a, st, w.l, scanned_e, scanned_v);
+        else pull_level<OffT, PARENT, STATS>(a, st, w.l, scanned_e, scanned_v);
         if (STATS) {
             scanned_e = warp_sum(scanned_e);
             scanned_v = warp_sum(scanned_v);
@@ -767,6 +926,8 @@ __device__ void init_phase(const BfsArgs<OffT> &a, const LevelState &st0) {
         a.ctl->qpack[0] = st0.q ? ((1ull << 32) | st0.T) : 0ull;
         for (int i = 1; i < 4; ++i) a.ctl->qpack[i] = 0ull;
         a.ctl->cpack = 0ull;
+        for (int i = 0; i < 4; ++i) a.ctl->wq[i] = 0u;
+        for (int i = 0; i < 4; ++i) a.ctl->ucount[i] = 0u;
     }
 }
 
@@ -889,6 +1050,10 @@ BfsArgs<OffT> make_args(grx_graph *g, int32_t src, int32_t *depth, int32_t *pare
         const double t = pb * (double)g->nv;
         a.bmp_min_T = t < 1.0 ? 1u : (t > 4294967295.0 ? 0xffffffffu : (uint32_t)t);
     }
+    a.U[0] = g->ulist[0];
+    a.U[1] = g->ulist[1];
+    a.first2 = g->first2;
+    a.ulist_max = (uint32_t)(g->nv / 64 > 0 ? g->nv / 64 : 1);
     a.timeout_ns = grx_timeout_ns(o);
     a.src = src;
     return a;

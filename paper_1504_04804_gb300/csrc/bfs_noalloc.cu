@@ -8,7 +8,7 @@
 // path that may not fail with out-of-memory half-way.  bfs_noalloc serves
 // them: the caller passes the CSR arrays and the output arrays (all device
 // memory it owns), and every piece of traversal scratch -- frontier queues,
-// bitmaps, the control block -- lives in one file-scope
+// bitmaps, candidate lists, the control block -- lives in one file-scope
 // __device__ array of fixed size, reserved when the library is loaded and held
 // by every GPU that loads it until the process exits.
 //
@@ -35,6 +35,7 @@ struct NoallocScratch {
     int32_t qv[3][kMaxNv];
     uint32_t qe[3][kMaxNv];
     int32_t qr[3][kMaxNv];
+    int32_t ulist[2][kMaxNv];
 };
 static_assert(sizeof(NoallocScratch) == GRX_NOALLOC_SCRATCH_BYTES,
               "grx.h states the size of the fixed scratch array");
@@ -148,6 +149,8 @@ extern "C" grx_status bfs_noalloc(int64_t nv, int64_t ne, const int32_t *row_off
         g.qe[i] = sc->qe[i];
         g.qr[i] = sc->qr[i];
     }
+    g.ulist[0] = sc->ulist[0];
+    g.ulist[1] = sc->ulist[1];
     g.ctl = &sc->ctl;
     g.bar_flags = sc->bar_flags;
     g.ws_ready = 1;

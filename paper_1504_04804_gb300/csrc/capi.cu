@@ -322,16 +322,19 @@ grx_status grx_ensure_workspace(grx_graph *g, cudaStream_t s) {
         g->qr[i] = grx_alloc(g, nv * (g->off64 ? 8 : 4), s);
     }
     for (int i = 0; i < 2; ++i) g->ulist[i] = (int32_t *)grx_alloc(g, nv * 4, s);
+    g->first2 = (int2 *)grx_alloc(g, nv * sizeof(int2), s);
     g->ctl = (TravCtl *)grx_alloc(g, sizeof(TravCtl), s);
     g->bar_flags = (unsigned int *)grx_alloc(g, sizeof(unsigned int) * GRX_MAX_GRID, s);
     g->stats = (DevStats *)grx_alloc(g, sizeof(DevStats), s);
     g->stamp = (int32_t *)grx_alloc(g, nv * 4, s);
-    bool ok = g->visited && g->ctl && g->bar_flags && g->stats && g->stamp;
+    bool ok = g->visited && g->ctl && g->bar_flags && g->stats && g->stamp && g->first2;
     for (int i = 0; i < 3; ++i) ok = ok && g->fbits[i] && g->qv[i] && g->qe[i] && g->qr[i];
     for (int i = 0; i < 2; ++i) ok = ok && g->ulist[i];
     if (!ok) return grx_fail(GRX_ENOMEM, "traversal workspace allocation failed (nv=%d)", g->nv);
     GRX_CUDA(cudaMemsetAsync(g->ctl, 0, sizeof(TravCtl), s));
     GRX_CUDA(cudaMemsetAsync(g->stats, 0, sizeof(DevStats), s));
+    grx_status st = grx_build_first2(g, s);
+    if (st != GRX_OK) return st;
     g->ws_ready = 1;
     return GRX_OK;
 }

@@ -35,7 +35,8 @@ struct alignas(128) TravCtl {
     unsigned int farcnt[2];          // SSSP near-far: far pile lengths (ping-pong)
     unsigned int farmin[2];          // SSSP near-far: smallest distance in the far pile (by pile)
     unsigned int bcfix[3];           // BC backward: rows finished after the barrier, by level mod 3
-    unsigned int pad0[6];
+    unsigned int wq[4];              // BFS: chunk counters of the word-owning sweeps, ring by phase
+    unsigned int pad0[2];
     unsigned int bar_count;          // grid barrier arrivals
     unsigned int pad1[31];
     unsigned int bar_gen;            // grid barrier generation
@@ -96,6 +97,7 @@ struct grx_graph {
     uint32_t *qe[3];                 // exclusive edge prefix per frontier slot
     void *qr[3];                     // row start (OffT) per frontier slot
     int32_t *ulist[2];               // unvisited lists [nv] each
+    int2 *first2;                    // [nv] first two neighbours of each row (-1 = none)
     TravCtl *ctl;
     unsigned int *bar_flags;         // [GRX_MAX_GRID] per-block arrival flags
     DevStats *stats;
@@ -158,6 +160,8 @@ grx_status grx_cuda_fail(cudaError_t e, const char *what);
 
 // Builds g->active / g->aoff / g->n_active (synchronises s once).
 grx_status grx_build_active(grx_graph *g, cudaStream_t s);
+// Fills g->first2 (allocated by the caller) from the CSR.
+grx_status grx_build_first2(grx_graph *g, cudaStream_t s);
 // Cached (first active row, row count) of every tile of `tile` consecutive
 // edges over the whole edge array.
 grx_status grx_edge_tiles(grx_graph *g, int tile, cudaStream_t s, const int2 **out);

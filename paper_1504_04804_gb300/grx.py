@@ -363,7 +363,7 @@ def pagerank_block(g: Graph, shift: int):
 
 
 GRX_NOALLOC_MAX_NV = 1 << 19
-GRX_NOALLOC_SCRATCH_BYTES = 19219328
+GRX_NOALLOC_SCRATCH_BYTES = 23413632
 
 
 def _noalloc_tensor(name: str, t, numel: int | None = None):
