@@ -147,6 +147,7 @@ struct PullWarpSmem {
     uint32_t hofs[PULL_WCH + 1];   // heavy lists: prefix of the unresolved lengths
     alignas(16) uint16_t hrid[PULL_HSTEP];   // heavy step: list of each position
     int32_t hpar[PULL_WCH];        // heavy lists: parent found (-1: none yet)
+    uint16_t hv[PULL_WCH];         // heavy lists: the candidate (offset in its chunk)
     uint32_t fb[32];               // found bits of the chunk's words
 };
 
@@ -155,6 +156,18 @@ union WarpSmem {
     PushWarpSmem<OffT> p;
     PullWarpSmem<OffT> l;
 };
+
+// Each warp's shared memory, in the block's dynamic shared memory (WARPS
+// entries; more than the 48 KB a block may declare statically with 64-bit
+// offsets, so the kernels opt in to the larger size before their first launch).
+template <typename OffT>
+constexpr size_t bfs_smem_bytes() { return WARPS * sizeof(WarpSmem<OffT>); }
+
+template <typename OffT>
+__device__ __forceinline__ WarpSmem<OffT> &warp_smem() {
+    extern __shared__ __align__(16) unsigned char bfs_dsmem[];
+    return reinterpret_cast<WarpSmem<OffT> *>(bfs_dsmem)[threadIdx.x >> 5];
+}
 
 __device__ __forceinline__ int level_phases(const LevelState &s) {
     return s.dir == DIR_PULL ? 1 : 1 + s.compact + s.bmp;
@@ -511,7 +524,7 @@ __device__ void bitmap_to_queue(const BfsArgs<OffT> &a, const LevelState &st, Pu
 
 // Row start, degree and first two neighbours of the candidates a lane takes
 // in the round starting at list entry `base` (entries base + k*32 + lane;
-// vertex = origin + list[i]); the three loads of a candidate are independent.
+// vertex = origin + list[i]).
 template <typename OffT>
 __device__ __forceinline__ void load_candidates(const BfsArgs<OffT> &a, int64_t origin, const uint16_t *list,
                                                 int base, int n, int32_t (&v)[PULL_PER_LANE],
@@ -534,26 +547,20 @@ __device__ __forceinline__ void load_candidates(const BfsArgs<OffT> &a, int64_t 
     }
 }
 
-// One pull round over up to PULL_WCH candidates of a warp (lane holds
-// candidates k*32 + lane): v (-1 = empty slot), row start b, degree deg.
-//  light phase: the first PULL_LIGHT neighbours of every candidate, all in
-//     flight at once;
-//  heavy phase: the lists without a hit yet are concatenated and consumed
-//     front to back in load-balanced steps of PULL_HSTEP edges shared by the
-//     whole warp; a list leaves once any of its edges hits the frontier (any
-//     frontier neighbour is a valid parent: edge skipping).
-// Returns in par[k] the parent found (-1: none).  F_L is read-only during the
-// level, so its probes may be served by L1 (hot words of high-degree vertices
-// are then not refetched from L2 by every warp).
+// Light phase of a pull round over up to PULL_WCH candidates of a warp (lane
+// holds candidates k*32 + lane): v (-1 = empty slot), row start b, degree
+// deg, first two neighbours f2.  The first PULL_LIGHT neighbours of every
+// candidate are probed against F_L, all in flight at once.  par[k] = the
+// parent found (-1: none); bit k of the result = candidate k still needs its
+// remaining neighbours (heavy).  F_L is read-only during the level, so its
+// probes may be served by L1 (hot words of high-degree vertices are then not
+// refetched from L2 by every warp).
 template <typename OffT, bool STATS>
-__device__ __forceinline__ void pull_round(const BfsArgs<OffT> &a, const uint32_t *Fin,
-                                           PullWarpSmem<OffT> &w, const int32_t (&v)[PULL_PER_LANE],
-                                           const OffT (&b)[PULL_PER_LANE],
-                                           const uint32_t (&deg)[PULL_PER_LANE],
-                                           const int2 (&f2)[PULL_PER_LANE],
-                                           int32_t (&par)[PULL_PER_LANE],
-                                           unsigned long long &scanned_e, unsigned long long &scanned_v) {
-    const unsigned int lane = threadIdx.x & 31;
+__device__ __forceinline__ uint32_t pull_light(const BfsArgs<OffT> &a, const uint32_t *Fin,
+                                               const int32_t (&v)[PULL_PER_LANE], const OffT (&b)[PULL_PER_LANE],
+                                               const uint32_t (&deg)[PULL_PER_LANE],
+                                               const int2 (&f2)[PULL_PER_LANE], int32_t (&par)[PULL_PER_LANE],
+                                               unsigned long long &scanned_e, unsigned long long &scanned_v) {
     static_assert(PULL_LIGHT == 2, "the light phase probes the two neighbours of first2");
     int32_t u0[PULL_PER_LANE], u1[PULL_PER_LANE];
 #pragma unroll
@@ -584,8 +591,17 @@ __device__ __forceinline__ void pull_round(const BfsArgs<OffT> &a, const uint32_
         }
         if (v[k] >= 0 && par[k] < 0 && deg[k] > PULL_LIGHT) heavy |= 1u << k;
     }
-    int nh = 0;
-    int hpos[PULL_PER_LANE];
+    return heavy;
+}
+
+// Appends the heavy candidates (bit k of `heavy`) to the warp's pending heavy
+// lists after the nh already there: next edge, edges left, no parent yet, the
+// vertex's offset in its 1,024-vertex chunk.  hpos[k] = entry of candidate k.  Returns the new
+// count (warp-uniform; at most PULL_WCH, which the caller guarantees).
+template <typename OffT>
+__device__ __forceinline__ int heavy_add(PullWarpSmem<OffT> &w, int nh, uint32_t heavy,
+                                         const int32_t (&v)[PULL_PER_LANE], const OffT (&b)[PULL_PER_LANE],
+                                         const uint32_t (&deg)[PULL_PER_LANE], int (&hpos)[PULL_PER_LANE]) {
 #pragma unroll
     for (int k = 0; k < PULL_PER_LANE; ++k) {
         const unsigned int m = __ballot_sync(GRX_FULL_MASK, heavy >> k & 1u);
@@ -594,10 +610,23 @@ __device__ __forceinline__ void pull_round(const BfsArgs<OffT> &a, const uint32_
             w.hb[hpos[k]] = b[k] + PULL_LIGHT;
             w.hl[hpos[k]] = deg[k] - PULL_LIGHT;
             w.hpar[hpos[k]] = -1;
+            w.hv[hpos[k]] = (uint16_t)(v[k] & (SC_VERTS - 1));
         }
         nh += __popc(m);
     }
     __syncwarp();
+    return nh;
+}
+
+// Heavy phase over the warp's nh pending lists: they are concatenated and
+// consumed front to back in load-balanced steps of PULL_HSTEP edges shared by
+// the whole warp; a list leaves once any of its edges hits the frontier (any
+// frontier neighbour is a valid parent: edge skipping).  On return w.hpar[h]
+// holds each list's parent (-1: none).
+template <typename OffT, bool STATS>
+__device__ __forceinline__ void heavy_run(const BfsArgs<OffT> &a, const uint32_t *Fin, PullWarpSmem<OffT> &w,
+                                          int nh, unsigned long long &scanned_e) {
+    const unsigned int lane = threadIdx.x & 31;
     while (nh > 0) {
         // exclusive prefix of the unresolved lengths; lane owns entries lane*PULL_PER_LANE + r
         uint32_t ln[PULL_PER_LANE], lsum = 0;
@@ -656,10 +685,6 @@ __device__ __forceinline__ void pull_round(const BfsArgs<OffT> &a, const uint32_
         }
         __syncwarp();
     }
-#pragma unroll
-    for (int k = 0; k < PULL_PER_LANE; ++k)
-        if (heavy >> k & 1u) par[k] = w.hpar[hpos[k]];
-    __syncwarp();
 }
 
 // Appends the vertices of bit set `bits` (lane holds word wd = word index of
@@ -682,10 +707,14 @@ __device__ __forceinline__ void warp_append_bits(uint32_t bits, int64_t sc, Pull
 // a frontier parent for the chunk's unvisited non-isolated vertices and
 // writes the chunk's visited and F_{L+1} words (and, with fclear, zeroes its
 // F_{L-1} words).  Chunks come from the phase's counter.  Candidates are
-// compacted in shared memory and probed PULL_WCH per round (pull_round); the
-// found vertices are labelled and their bits collect in the chunk's masks.
-// The candidates left unfound form the list U_{L+1} (in chunk order), which a
-// following pull level may work on instead of sweeping again.
+// compacted in shared memory and probed PULL_WCH per round (pull_light); the
+// lists still unresolved after their first neighbours wait in the warp's
+// pending heavy lists, which are scanned together (heavy_run) when the next
+// round could overflow them and at the end of the chunk, so a chunk usually
+// takes one heavy scan instead of one per round.  Found vertices are labelled
+// and their bits collect in the chunk's masks.  The candidates left unfound
+// form the list U_{L+1} (in chunk order), which a following pull level may
+// work on instead of sweeping again.
 template <typename OffT, bool PARENT, bool STATS>
 __device__ void pull_level(const BfsArgs<OffT> &a, const LevelState &st, PullWarpSmem<OffT> &w,
                            unsigned long long &scanned_e, unsigned long long &scanned_v) {
@@ -716,12 +745,35 @@ __device__ void pull_level(const BfsArgs<OffT> &a, const LevelState &st, PullWar
         if (own && st.fclear) Fold[wd] = 0u;
         w.fb[lane] = 0u;
         const int n = warp_compact_bits(cand, w.list);
+        const int64_t origin = sc * SC_VERTS;
         int32_t vn[PULL_PER_LANE];
         OffT bn[PULL_PER_LANE];
         uint32_t dn[PULL_PER_LANE];
         int2 fn[PULL_PER_LANE];
-        load_candidates(a, sc * SC_VERTS, w.list, 0, n, vn, bn, dn, fn);
-        for (int base = 0; base < n; base += PULL_WCH) {
+        load_candidates(a, origin, w.list, 0, n, vn, bn, dn, fn);
+        // the chunk's pending heavy lists: scanned, then their found vertices
+        // labelled like the light ones
+        int nh = 0;
+        auto flush_heavy = [&]() {
+            heavy_run<OffT, STATS>(a, Fin, w, nh, scanned_e);
+            for (int h = (int)lane; h < nh; h += 32) {
+                const int32_t p = w.hpar[h];
+                if (p >= 0) {
+                    const int32_t u = (int32_t)(origin + w.hv[h]);
+                    a.depth[u] = L + 1;
+                    if (PARENT) a.parent[u] = p;
+                    atomicOr(&w.fb[(u >> 5) & 31], 1u << (u & 31));
+                    nfound += 1;
+                    nedges += (uint32_t)(__ldg(a.ro + u + 1) - __ldg(a.ro + u));
+                }
+            }
+            __syncwarp();
+            nh = 0;
+        };
+        // one flush site: before a round whose heavy lists could overflow the
+        // pending ones, and after the last round
+        for (int base = 0;; base += PULL_WCH) {
+            const bool more = base < n;
             int32_t v[PULL_PER_LANE];
             OffT b[PULL_PER_LANE];
             uint32_t deg[PULL_PER_LANE];
@@ -734,12 +786,20 @@ __device__ void pull_level(const BfsArgs<OffT> &a, const LevelState &st, PullWar
                 f2[k] = fn[k];
             }
             int32_t par[PULL_PER_LANE];
-            pull_round<OffT, STATS>(a, Fin, w, v, b, deg, f2, par, scanned_e, scanned_v);
-            load_candidates(a, sc * SC_VERTS, w.list, base + PULL_WCH, n, vn, bn, dn, fn);
+            uint32_t heavy = 0;
+            int nnew = 0;
+            if (more) {
+                heavy = pull_light<OffT, STATS>(a, Fin, v, b, deg, f2, par, scanned_e, scanned_v);
+                nnew = (int)warp_sum((uint32_t)__popc(heavy));
+            }
+            if (!more || nh + nnew > PULL_WCH) flush_heavy();
+            if (!more) break;
+            // the next round's loads go out and travel while this round is labelled
+            load_candidates(a, origin, w.list, base + PULL_WCH, n, vn, bn, dn, fn);
             // label the found vertices; their bits go to the chunk's word masks
 #pragma unroll
             for (int k = 0; k < PULL_PER_LANE; ++k) {
-                if (v[k] >= 0 && par[k] >= 0) {
+                if (par[k] >= 0) {
                     a.depth[v[k]] = L + 1;
                     if (PARENT) a.parent[v[k]] = par[k];
                     atomicOr(&w.fb[(v[k] >> 5) & 31], 1u << (v[k] & 31));
@@ -747,7 +807,8 @@ __device__ void pull_level(const BfsArgs<OffT> &a, const LevelState &st, PullWar
                     nedges += deg[k];
                 }
             }
-            __syncwarp();
+            int hpos[PULL_PER_LANE];
+            nh = heavy_add(w, nh, heavy, v, b, deg, hpos);
         }
         const uint32_t fb = w.fb[lane];
         if (own) {
@@ -766,7 +827,7 @@ __device__ void pull_level(const BfsArgs<OffT> &a, const LevelState &st, PullWar
 
 // Pull level over the list U_L of the candidates the previous pull level
 // left unfound (every one unvisited and non-isolated): slices of PULL_WCH
-// list entries per warp, one pull_round each.  Found vertices are labelled,
+// list entries per warp, light probes then the heavy lists of the slice.  Found vertices are labelled,
 // their bits set in visited and F_{L+1} (reductions: a word is shared with
 // other warps' vertices), and they are appended to Q_{L+1} with their degrees
 // and row starts, so a push level that follows needs no compaction.  The
@@ -814,7 +875,14 @@ __device__ void pull_list(const BfsArgs<OffT> &a, const LevelState &st, PullWarp
             deg[k] = (uint32_t)(e - b[k]);
         }
         int32_t par[PULL_PER_LANE];
-        pull_round<OffT, STATS>(a, Fin, w, v, b, deg, f2, par, scanned_e, scanned_v);
+        const uint32_t heavy = pull_light<OffT, STATS>(a, Fin, v, b, deg, f2, par, scanned_e, scanned_v);
+        int hpos[PULL_PER_LANE];
+        const int nh = heavy_add(w, 0, heavy, v, b, deg, hpos);
+        heavy_run<OffT, STATS>(a, Fin, w, nh, scanned_e);
+#pragma unroll
+        for (int k = 0; k < PULL_PER_LANE; ++k)
+            if (heavy >> k & 1u) par[k] = w.hpar[hpos[k]];
+        __syncwarp();
         uint32_t app = 0, left = 0;
 #pragma unroll
         for (int k = 0; k < PULL_PER_LANE; ++k) {
@@ -934,8 +1002,7 @@ __device__ void init_phase(const BfsArgs<OffT> &a, const LevelState &st0) {
 template <typename OffT, bool PARENT, bool STATS>
 __global__ void __launch_bounds__(BFS_BLOCK, GRX_BFS_MIN_BLOCKS) k_bfs_persistent(BfsArgs<OffT> a) {
     __shared__ LevelState s_st;
-    __shared__ WarpSmem<OffT> wsm[WARPS];
-    WarpSmem<OffT> &w = wsm[threadIdx.x >> 5];
+    WarpSmem<OffT> &w = warp_smem<OffT>();
     FlagBarrier bar{a.bar_flags, &a.ctl->bar_release, a.ctl, a.timeout_ns, 0u};
     if (threadIdx.x == 0) s_st = initial_state(a);
     __syncthreads();
@@ -962,7 +1029,6 @@ __global__ void __launch_bounds__(BFS_BLOCK, GRX_BFS_MIN_BLOCKS) k_bfs_persisten
 template <typename OffT, bool PARENT, bool STATS>
 __global__ void __launch_bounds__(BFS_BLOCK) k_bfs_step(BfsArgs<OffT> a, int launch) {
     __shared__ LevelState s_st;
-    __shared__ WarpSmem<OffT> wsm[WARPS];
     static_assert(sizeof(LevelState) <= sizeof(long long) * 8, "state must fit hstate");
     if (launch == 0) {
         if (threadIdx.x == 0) s_st = initial_state(a);
@@ -986,7 +1052,7 @@ __global__ void __launch_bounds__(BFS_BLOCK) k_bfs_step(BfsArgs<OffT> a, int lau
         if (st.done) a.ctl->levels_run = st.L;
     }
     if (st.done) return;
-    run_phase<OffT, PARENT, STATS>(a, st, wsm[threadIdx.x >> 5]);
+    run_phase<OffT, PARENT, STATS>(a, st, warp_smem<OffT>());
 }
 
 // CUDA-graph variant: the body of a device-evaluated WHILE node is one phase
@@ -996,13 +1062,12 @@ __global__ void __launch_bounds__(BFS_BLOCK) k_bfs_step(BfsArgs<OffT> a, int lau
 template <typename OffT, bool PARENT>
 __global__ void __launch_bounds__(BFS_BLOCK) k_bfs_glevel(const BfsArgs<OffT> *ap) {
     __shared__ LevelState s_st;
-    __shared__ WarpSmem<OffT> wsm[WARPS];
     const BfsArgs<OffT> &a = *ap;
     if (threadIdx.x == 0) memcpy(&s_st, (const void *)a.ctl->hstate[0], sizeof(LevelState));
     __syncthreads();
     const LevelState st = s_st;
     if (st.done) return;
-    run_phase<OffT, PARENT, false>(a, st, wsm[threadIdx.x >> 5]);
+    run_phase<OffT, PARENT, false>(a, st, warp_smem<OffT>());
 }
 
 template <typename OffT>
@@ -1014,6 +1079,25 @@ __global__ void k_bfs_gtick(const BfsArgs<OffT> *ap, cudaGraphConditionalHandle 
     memcpy((void *)a.ctl->hstate[0], &ns, sizeof ns);
     if (ns.done) a.ctl->levels_run = ns.L;
     cudaGraphSetConditional(h, ns.done ? 0u : 1u);
+}
+
+// Opt every kernel of an instantiation in to its dynamic shared memory size
+// (once per process).
+template <typename OffT, bool PARENT, bool STATS>
+grx_status prepare_kernels() {
+    static bool done = false;
+    if (done) return GRX_OK;
+    const int bytes = (int)bfs_smem_bytes<OffT>();
+    GRX_CUDA(cudaFuncSetAttribute((const void *)k_bfs_persistent<OffT, PARENT, STATS>,
+                                  cudaFuncAttributeMaxDynamicSharedMemorySize, bytes));
+    GRX_CUDA(cudaFuncSetAttribute((const void *)k_bfs_step<OffT, PARENT, STATS>,
+                                  cudaFuncAttributeMaxDynamicSharedMemorySize, bytes));
+    GRX_CUDA(cudaFuncSetAttribute((const void *)k_bfs_step<OffT, PARENT, false>,
+                                  cudaFuncAttributeMaxDynamicSharedMemorySize, bytes));
+    GRX_CUDA(cudaFuncSetAttribute((const void *)k_bfs_glevel<OffT, PARENT>,
+                                  cudaFuncAttributeMaxDynamicSharedMemorySize, bytes));
+    done = true;
+    return GRX_OK;
 }
 
 template <typename OffT>
@@ -1091,6 +1175,7 @@ grx_status graph_exec(grx_graph *g, cudaGraphExec_t *out) {
         k1.func = (void *)k_bfs_glevel<OffT, PARENT>;
         k1.gridDim = dim3(g->ctx->num_sms * 3);
         k1.blockDim = dim3(BFS_BLOCK);
+        k1.sharedMemBytes = (unsigned int)bfs_smem_bytes<OffT>();
         k1.kernelParams = a1;
         e = cudaGraphAddKernelNode(&n1, body, nullptr, 0, &k1);
         cudaKernelNodeParams k2 = {};
@@ -1115,6 +1200,9 @@ template <typename OffT, bool PARENT, bool STATS>
 grx_status launch_typed(grx_graph *g, int32_t src, int32_t *depth, int32_t *parent,
                         const grx_opts *o, cudaStream_t s) {
     BfsArgs<OffT> a = make_args<OffT>(g, src, depth, parent, o);
+    grx_status pst = prepare_kernels<OffT, PARENT, STATS>();
+    if (pst != GRX_OK) return pst;
+    const size_t smem = bfs_smem_bytes<OffT>();
     if (o->loop == GRX_LOOP_GRAPH) {
         if (STATS) return grx_fail(GRX_EINVAL, "bfs: collect_stats needs the persistent or host loop");
         cudaGraphExec_t ex = nullptr;
@@ -1124,7 +1212,7 @@ grx_status launch_typed(grx_graph *g, int32_t src, int32_t *depth, int32_t *pare
         // initialisation launch and the level loop
         GRX_CUDA(cudaMemcpyAsync(g->bfs_gargs, &a, sizeof a, cudaMemcpyHostToDevice, s));
         if (o->ev_begin) GRX_CUDA(cudaEventRecord((cudaEvent_t)o->ev_begin, s));
-        k_bfs_step<OffT, PARENT, false><<<g->ctx->num_sms * 3, BFS_BLOCK, 0, s>>>(a, 0);
+        k_bfs_step<OffT, PARENT, false><<<g->ctx->num_sms * 3, BFS_BLOCK, smem, s>>>(a, 0);
         GRX_CUDA(cudaGetLastError());
         GRX_CUDA(cudaGraphLaunch(ex, s));
         if (o->ev_end) GRX_CUDA(cudaEventRecord((cudaEvent_t)o->ev_end, s));
@@ -1138,7 +1226,7 @@ grx_status launch_typed(grx_graph *g, int32_t src, int32_t *depth, int32_t *pare
         if (o->ev_begin) GRX_CUDA(cudaEventRecord((cudaEvent_t)o->ev_begin, s));
         const long long max_launch = 3ll * ((long long)g->nv + 1) + 1;
         for (long long launch = 0; launch <= max_launch; ++launch) {
-            k_bfs_step<OffT, PARENT, STATS><<<blocks, BFS_BLOCK, 0, s>>>(a, (int)launch);
+            k_bfs_step<OffT, PARENT, STATS><<<blocks, BFS_BLOCK, smem, s>>>(a, (int)launch);
             if ((launch & 15) == 15) {
                 GRX_CUDA(cudaMemcpyAsync(st_host, (const void *)g->ctl->hstate[launch & 1],
                                          sizeof st_host, cudaMemcpyDeviceToHost, s));
@@ -1155,7 +1243,7 @@ grx_status launch_typed(grx_graph *g, int32_t src, int32_t *depth, int32_t *pare
     static int max_blocks_per_sm = -1;
     if (max_blocks_per_sm < 0) {
         GRX_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(
-            &max_blocks_per_sm, k_bfs_persistent<OffT, PARENT, STATS>, BFS_BLOCK, 0));
+            &max_blocks_per_sm, k_bfs_persistent<OffT, PARENT, STATS>, BFS_BLOCK, smem));
         if (max_blocks_per_sm < 1)
             return grx_fail(GRX_ECUDA, "bfs: persistent kernel does not fit on an SM");
     }
@@ -1167,7 +1255,7 @@ grx_status launch_typed(grx_graph *g, int32_t src, int32_t *depth, int32_t *pare
     void *args[] = {(void *)&a};
     if (o->ev_begin) GRX_CUDA(cudaEventRecord((cudaEvent_t)o->ev_begin, s));
     GRX_CUDA(cudaLaunchCooperativeKernel((const void *)k_bfs_persistent<OffT, PARENT, STATS>,
-                                         dim3(blocks), dim3(BFS_BLOCK), args, 0, s));
+                                         dim3(blocks), dim3(BFS_BLOCK), args, smem, s));
     if (o->ev_end) GRX_CUDA(cudaEventRecord((cudaEvent_t)o->ev_end, s));
     return GRX_OK;
 }
