@@ -205,22 +205,29 @@ class ClockSampler:
 
 
 def _captured_traffic(workload: str):
-    """DRAM bytes per traversal launch from the committed ncu summary, if it
-    was taken on this workload and the kernel sources are unchanged since."""
+    """DRAM bytes per traversal launch from the committed ncu summary of this
+    workload (profiles/k_bfs_persistent_<workload>_dram.md), if the kernel
+    sources are unchanged since it was taken."""
     import hashlib
     import re
     try:
-        text = open(os.path.join(ROOT, "profiles", "k_bfs_persistent_rmat22_dram.md")).read()
+        text = open(os.path.join(ROOT, "profiles", f"k_bfs_persistent_{workload}_dram.md")).read()
         wl = re.search(r"^workload: (\S+)", text, re.M).group(1)
         tb = int(re.search(r"^traffic_bytes_per_launch: (\d+)", text, re.M).group(1))
         sh = re.search(r"^source_sha1: ([0-9a-f]+)", text, re.M).group(1)
-        csrc = os.path.join(ROOT, "paper_1504_04804_gb300", "csrc")
-        src = b"".join(open(os.path.join(csrc, f), "rb").read() for f in ("bfs.cu", "grx_internal.cuh"))
-        if wl == workload and hashlib.sha1(src).hexdigest()[:16] == sh:
+        if wl == workload and bfs_source_sha() == sh:
             return tb
     except Exception:
         pass
     return None
+
+
+def bfs_source_sha() -> str:
+    """First 16 hex digits of the sha1 of the traversal kernel's sources."""
+    import hashlib
+    csrc = os.path.join(ROOT, "paper_1504_04804_gb300", "csrc")
+    src = b"".join(open(os.path.join(csrc, f), "rb").read() for f in ("bfs.cu", "grx_internal.cuh"))
+    return hashlib.sha1(src).hexdigest()[:16]
 
 
 def world_rate(units: float, seconds: float, device="cpu"):
@@ -331,10 +338,16 @@ def main():
     ap.add_argument("--cpu-budget", type=float, default=15.0,
                     help="seconds of oracle BFS for the cpu_baseline sample")
     ap.add_argument("--no-extra", action="store_true", help="skip SSSP/CC/PageRank timings")
-    ap.add_argument("--serving-queries", type=int, default=1000,
+    ap.add_argument("--serving-queries", type=int, default=800,
                     help="queries per offered-load point of the serving measurement")
     ap.add_argument("--no-tune", action="store_true",
                     help="use the paper's switch rule with --alpha/--beta instead of the autotuner")
+    ap.add_argument("--tune-cache", default=None,
+                    help="autotuner cache file (default: the autotuner's per-user cache)")
+    ap.add_argument("--rmat26-steps", type=int, default=3,
+                    help="timed steps of the R-MAT 26 leg (0 = skip it)")
+    ap.add_argument("--cpu-budget26", type=float, default=10.0,
+                    help="seconds of oracle BFS for the R-MAT 26 leg's cpu_baseline sample")
     args = ap.parse_args()
     if args.impl == "reference":
         return reference_arm(args)
@@ -364,131 +377,39 @@ def main():
     ro_h = ro.cpu().numpy()
     srcs = [int(s) for s in inputs.pick_sources(ro_h, N_SOURCES, SOURCE_SEED)]
     deg_h = np.diff(ro_h)
-
-    # autotuned switch rule / alpha / beta / grid on separate tuning sources
-    # (seed 2, not the measured ones); tuning time is reported, not timed
-    tuned = None
-    knobs = {"alpha": args.alpha, "beta": args.beta, "exact_fv": 0, "grid_blocks": 0}
-    if not args.no_tune:
-        from paper_1504_04804_gb300 import autotune
-        tuned = autotune.tune_bfs(g, ro_h, cache=None)
-        knobs = {k: tuned[k] for k in ("alpha", "beta", "exact_fv", "grid_blocks")}
-
-    # untimed instrumented pass: per-source byte model and TEPS numerator
-    st_opts = grx.opts(collect_stats=1, **knobs)
-    per_src = {}
-    for s in srcs:
-        d = grx.bfs(g, s, opts=st_opts)
-        st = grx.last_stats(g)
-        reached = d.cpu().numpy() >= 0
-        per_src[s] = {"edges": int(deg_h[reached].sum()), "bytes": bfs_bytes(st, nv, off_bytes),
-                      "levels": st["levels"], "dirs": "".join("PL"[x] for x in st["dir"])}
-    grx.graph_status(g)
-
     flush = torch.empty(256 << 20, dtype=torch.uint8, device=f"cuda:{dev}")
-    o = grx.opts(**knobs)
-    depth = torch.empty(nv, dtype=torch.int32, device=f"cuda:{dev}")
-    evs = [[torch.cuda.Event(enable_timing=True) for _ in range(4)]
-           for _ in range(args.steps * len(srcs))]
-    for ev in evs:              # torch creates the CUDA event on first record
-        for e in ev:
-            e.record(stream)
-
-    def traverse(s, ev=None):
-        if ev is not None:
-            o.ev_begin = ev[1].cuda_event
-            o.ev_end = ev[2].cuda_event
-            ev[0].record(stream)
-        else:
-            o.ev_begin = None
-            o.ev_end = None
-        grx.bfs(g, s, depth_out=depth, opts=o)
-        if ev is not None:
-            ev[3].record(stream)
-
-    for i in range(args.warmup):
-        for s in srcs:
-            flush.fill_(i & 0xff)
-            traverse(s)
-    torch.cuda.synchronize()
-    if ws > 1:
-        torch.distributed.barrier()
-    sampler = ClockSampler(dev)
-    time.sleep(0.3)
-    torch.cuda.synchronize()
-    t_wall0 = time.time()
-    k = 0
-    for step in range(args.steps):
-        for s in srcs:
-            flush.fill_(k & 0xff)
-            traverse(s, evs[k])
-            k += 1
-    torch.cuda.synchronize()
-    t_wall1 = time.time()
-    if ws > 1:
-        torch.distributed.barrier()
-    clocks = sampler.stop(t_wall0, t_wall1)
-    grx.graph_status(g)
-
-    step_ms = [e[0].elapsed_time(e[3]) for e in evs]        # whole bfs() call per traversal
-    kern_ms = [e[1].elapsed_time(e[2]) for e in evs]        # the traversal kernel alone
-    order = [s for _ in range(args.steps) for s in srcs]
-    edges_total = sum(per_src[s]["edges"] for s in order)
-    bytes_total = sum(per_src[s]["bytes"] for s in order)
-    t_total = sum(step_ms) / 1e3
-    rate, t_max = world_rate(float(edges_total), t_total, device=f"cuda:{dev}")
-    gteps = rate / 1e9
     peak, peak_kind = _peaks()
-    achieved = bytes_total / (sum(kern_ms) / 1e3) / 1e9
 
-    # end to end through the public API with host buffers: the source goes in
-    # as a kernel argument, the depth array comes back to pinned host memory.
-    host_depth = torch.empty(nv, dtype=torch.int32, pin_memory=True)
-    e2e_t = 0.0
-    e2e_edges = 0
-    o.ev_begin = None
-    o.ev_end = None
-    torch.cuda.synchronize()
-    for step in range(max(1, args.steps // 2)):
-        for s in srcs:
-            flush.fill_(step & 0xff)
-            torch.cuda.synchronize()
-            t0 = time.perf_counter()
-            grx.bfs(g, s, depth_out=depth, opts=o)
-            host_depth.copy_(depth, non_blocking=True)
-            torch.cuda.current_stream().synchronize()
-            e2e_t += time.perf_counter() - t0
-            e2e_edges += per_src[s]["edges"]
-    e2e = {"value": e2e_edges / e2e_t / 1e9, "unit": "GTEPS", "h2d_bytes_per_step": 4 * len(srcs),
-           "d2h_bytes_per_step": 4 * nv * len(srcs)}
+    knobs, tuned = tuned_knobs(args, g, ro_h)
+    m = measure_bfs(grx, torch, g, ro_h, srcs, knobs, args.steps, args.warmup, off_bytes, flush,
+                    stream, dev, ws, e2e_steps=max(1, args.steps // 2))
+    rate, t_max = world_rate(float(m["edges_total"]), m["t_total"], device=f"cuda:{dev}")
+    gteps = rate / 1e9
 
     if rank == 0:
-        print(f"[bench] {args.workload}: {gteps:.1f} GTEPS, kernel {statistics.median(kern_ms):.3f} ms, "
-              f"roofline {achieved / peak:.4f}, e2e {e2e['value']:.1f} GTEPS", file=sys.stderr, flush=True)
+        print(f"[bench] {args.workload}: {gteps:.1f} GTEPS, kernel {m['kernel_ms_median']:.3f} ms, "
+              f"roofline {m['achieved'] / peak:.4f}, e2e {m['e2e']['value']:.1f} GTEPS",
+              file=sys.stderr, flush=True)
     extra = {}
     if not args.no_extra:
         extra = other_primitives(grx, g, srcs, nv, ne, off_bytes, deg_h, flush, stream, peak,
-                                 ro_h=ro_h, col_dev=col)
+                                 ro_h=ro_h, col_dev=col, tune=not args.no_tune)
     if not args.no_extra and args.serving_queries > 0:
-        # serving: this graph plus two smaller resident R-MAT graphs
-        sgraphs, sdeg, sro = {f"rmat{cfg['scale']}": g}, {}, {f"rmat{cfg['scale']}": ro_h}
-        # a second handle (own workspace) of the two larger graphs lets the
-        # traversal-boundary server run two traversals of one graph at once
-        sreps = {f"rmat{cfg['scale']}": [grx.graph_load_csr(ro, col, w, offsets64=cfg["scale"] >= 26)]}
-        for sc in (18, 20):
-            r2, c2, w2 = grx.rmat_graph_device(sc, 16, seed=sc, wmax=64, weight_seed=100 + sc)
-            sgraphs[f"rmat{sc}"] = grx.graph_load_csr(r2, c2, w2)
-            sro[f"rmat{sc}"] = r2.cpu().numpy()
-            if sc == 20:
-                sreps[f"rmat{sc}"] = [grx.graph_load_csr(r2, c2, w2)]
-        for k, h in sro.items():
-            sdeg[k] = torch.from_numpy(np.diff(h).astype(np.int32)).cuda()
-        torch.cuda.empty_cache()
+        sgraphs, sdeg, sro, sreps = serving_graphs(grx, torch, cfg, g, ro, col, w, ro_h)
         try:
             extra["serving"] = serving_bench(sgraphs, sdeg, sro, n_queries=args.serving_queries,
                                              replicas=sreps)
         except Exception as e:        # reported, not fatal to the headline measurement
             extra["serving"] = {"error": f"{type(e).__name__}: {e}"}
+        del sgraphs, sreps
+        torch.cuda.empty_cache()
+    if not args.no_extra and args.workload != "rmat26" and args.rmat26_steps > 0:
+        try:
+            extra["rmat26"] = rmat26_leg(args, grx, torch, flush, stream, dev, peak, peak_kind,
+                                         rank == 0)
+        except Exception as e:        # reported, not fatal to the headline measurement
+            extra["rmat26"] = {"error": f"{type(e).__name__}: {e}"}
+        torch.cuda.empty_cache()
 
     cpu = None
     if rank == 0:
@@ -505,27 +426,251 @@ def main():
             "ms_per_step": t_max / args.steps * 1e3, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "int32", "data": "synthetic",
             "config": dict(_config(args, nv, ne, "int32" if off_bytes == 4 else "int64"), **knobs),
-            "autotune": None if tuned is None else {
-                "seconds": tuned["seconds"], "configs_tried": tuned["tried"],
-                "tuning_sources": tuned["tuning_sources"]},
-            "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
-                         "frac": achieved / peak, "traffic": _captured_traffic(args.workload),
+            "autotune": _autotune_block(tuned),
+            "roofline": {"bound": "hbm", "achieved": m["achieved"], "peak": peak, "unit": "GB/s",
+                         "frac": m["achieved"] / peak, "traffic": _captured_traffic(args.workload),
                          "kernel": "k_bfs_persistent", "peak_kind": peak_kind,
-                         "bytes_per_launch": bytes_total / len(order),
-                         "launch_ms": sum(kern_ms) / len(kern_ms)},
+                         "bytes_per_launch": m["bytes_per_launch"], "launch_ms": m["launch_ms"]},
             "cpu_baseline": cpu,
-            "e2e": e2e,
-            "gpu_launches": len(order),         # one persistent k_bfs_persistent per traversal
-            "clocks": clocks,
-            "detail": {"traversal_ms_median": statistics.median(step_ms),
-                       "kernel_ms_median": statistics.median(kern_ms),
-                       "levels": {str(s): per_src[s]["dirs"] for s in srcs[:4]}},
+            "e2e": m["e2e"],
+            "gpu_launches": m["launches"],      # one persistent k_bfs_persistent per traversal
+            "clocks": m["clocks"],
+            "detail": {"traversal_ms_median": m["traversal_ms_median"],
+                       "kernel_ms_median": m["kernel_ms_median"],
+                       "levels": {str(s): m["per_src"][s]["dirs"] for s in srcs[:4]}},
             "extra": extra,
         }
         print(json.dumps(line), flush=True)
     if ws > 1:
         torch.distributed.destroy_process_group()
     return 0
+
+
+def _autotune_block(tuned):
+    if tuned is None:
+        return None
+    return {"seconds": tuned["seconds"], "configs_tried": tuned["tried"], "cached": tuned["cached"],
+            "push_bitmap": tuned.get("push_bitmap", 0.0), "tuning_sources": tuned["tuning_sources"],
+            "cache_hit_on_second_lookup": tuned.get("second_lookup_cached")}
+
+
+def tuned_knobs(args, g, ro_h):
+    """The switch rule / alpha / beta / grid / push_bitmap the autotuner picks on
+    separate tuning sources (seed 2, not the measured ones), through its cache
+    (a second lookup must be a hit); tuning time is reported, not timed."""
+    knobs = {"alpha": args.alpha, "beta": args.beta, "exact_fv": 0, "grid_blocks": 0,
+             "push_bitmap": 0.0}
+    if args.no_tune:
+        return knobs, None
+    from paper_1504_04804_gb300 import autotune
+    cache = args.tune_cache or autotune.DEFAULT_CACHE
+    tuned = autotune.tune_bfs(g, ro_h, cache=cache)
+    tuned["second_lookup_cached"] = autotune.tune_bfs(g, ro_h, cache=cache)["cached"]
+    knobs = {k: tuned.get(k, 0) for k in ("alpha", "beta", "exact_fv", "grid_blocks", "push_bitmap")}
+    return knobs, tuned
+
+
+def measure_bfs(grx, torch, g, ro_h, srcs, knobs, steps, warmup, off_bytes, flush, stream, dev, ws,
+                e2e_steps=1):
+    """One instrumented pass per source (byte model, TEPS numerator), then
+    `warmup` untimed and `steps` timed steps of one traversal per source, L2
+    flushed before each, CUDA events around the whole call and around the
+    kernel, clocks sampled meanwhile; then the end-to-end number through the
+    public API with the depth array read back to pinned host memory."""
+    nv = g.nv
+    deg_h = np.diff(ro_h)
+    st_opts = grx.opts(collect_stats=1, **knobs)
+    per_src = {}
+    for s in srcs:
+        d = grx.bfs(g, s, opts=st_opts)
+        st = grx.last_stats(g)
+        reached = d.cpu().numpy() >= 0
+        per_src[s] = {"edges": int(deg_h[reached].sum()), "bytes": bfs_bytes(st, nv, off_bytes),
+                      "levels": st["levels"], "dirs": "".join("PL"[x] for x in st["dir"])}
+    grx.graph_status(g)
+    o = grx.opts(**knobs)
+    depth = torch.empty(nv, dtype=torch.int32, device=f"cuda:{dev}")
+    evs = [[torch.cuda.Event(enable_timing=True) for _ in range(4)] for _ in range(steps * len(srcs))]
+    for ev in evs:              # torch creates the CUDA event on first record
+        for e in ev:
+            e.record(stream)
+
+    def traverse(s, ev=None):
+        if ev is not None:
+            o.ev_begin = ev[1].cuda_event
+            o.ev_end = ev[2].cuda_event
+            ev[0].record(stream)
+        else:
+            o.ev_begin = None
+            o.ev_end = None
+        grx.bfs(g, s, depth_out=depth, opts=o)
+        if ev is not None:
+            ev[3].record(stream)
+
+    for i in range(warmup):
+        for s in srcs:
+            flush.fill_(i & 0xff)
+            traverse(s)
+    torch.cuda.synchronize()
+    if ws > 1:
+        torch.distributed.barrier()
+    sampler = ClockSampler(dev)
+    time.sleep(0.3)
+    torch.cuda.synchronize()
+    t_wall0 = time.time()
+    k = 0
+    for step in range(steps):
+        for s in srcs:
+            flush.fill_(k & 0xff)
+            traverse(s, evs[k])
+            k += 1
+    torch.cuda.synchronize()
+    t_wall1 = time.time()
+    if ws > 1:
+        torch.distributed.barrier()
+    clocks = sampler.stop(t_wall0, t_wall1)
+    grx.graph_status(g)
+    step_ms = [e[0].elapsed_time(e[3]) for e in evs]        # whole bfs() call per traversal
+    kern_ms = [e[1].elapsed_time(e[2]) for e in evs]        # the traversal kernel alone
+    order = [s for _ in range(steps) for s in srcs]
+    bytes_total = sum(per_src[s]["bytes"] for s in order)
+
+    # end to end through the public API with host buffers: the source goes in
+    # as a kernel argument, the depth array comes back to pinned host memory.
+    host_depth = torch.empty(nv, dtype=torch.int32, pin_memory=True)
+    e2e_t, e2e_edges = 0.0, 0
+    o.ev_begin = None
+    o.ev_end = None
+    torch.cuda.synchronize()
+    for step in range(e2e_steps):
+        for s in srcs:
+            flush.fill_(step & 0xff)
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            grx.bfs(g, s, depth_out=depth, opts=o)
+            host_depth.copy_(depth, non_blocking=True)
+            torch.cuda.current_stream().synchronize()
+            e2e_t += time.perf_counter() - t0
+            e2e_edges += per_src[s]["edges"]
+    return {"per_src": per_src, "edges_total": sum(per_src[s]["edges"] for s in order),
+            "t_total": sum(step_ms) / 1e3, "achieved": bytes_total / (sum(kern_ms) / 1e3) / 1e9,
+            "bytes_per_launch": bytes_total / len(order), "launch_ms": sum(kern_ms) / len(kern_ms),
+            "launches": len(order), "clocks": clocks,
+            "traversal_ms_median": statistics.median(step_ms),
+            "kernel_ms_median": statistics.median(kern_ms),
+            "e2e": {"value": e2e_edges / e2e_t / 1e9, "unit": "GTEPS", "h2d_bytes_per_step": 4 * len(srcs),
+                    "d2h_bytes_per_step": 4 * nv * len(srcs)}}
+
+
+def rmat26_leg(args, grx, torch, flush, stream, dev, peak, peak_kind, with_cpu):
+    """R-MAT scale 26 (int64 offsets, generated on the device): direction-
+    optimising BFS from the 16 seeded sources (the hot path's roofline target),
+    the 64-lane multi-source BFS with its own tuned knobs, and FP32 PageRank
+    (20 iterations); the oracle's BFS on one source as its CPU baseline."""
+    from paper_1504_04804_gb300 import autotune, inputs
+    cfg = RMAT_CONFIGS["rmat26"]
+    t0 = time.time()
+    ro, col, _ = grx.rmat_graph_device(cfg["scale"], cfg["edge_factor"], seed=cfg["seed"])
+    g = grx.graph_load_csr(ro, col, None, validate=False, offsets64=True)
+    torch.cuda.synchronize()
+    gen_s = time.time() - t0
+    nv, ne = g.nv, g.ne
+    ro_h = ro.cpu().numpy()
+    deg_h = np.diff(ro_h)
+    srcs = [int(s) for s in inputs.pick_sources(ro_h, N_SOURCES, SOURCE_SEED)]
+    knobs, tuned = tuned_knobs(args, g, ro_h)
+    m = measure_bfs(grx, torch, g, ro_h, srcs, knobs, args.rmat26_steps, 3, 8, flush, stream, dev, 1,
+                    e2e_steps=1)
+    # verbose fields first: the key numbers close the bench line
+    out = {"workload": "R-MAT scale 26 ef 16 (a,b,c,d=0.57,0.19,0.19,0.05, seed 26), int64 row offsets, "
+                       f"direction-optimising BFS from {N_SOURCES} seeded sources",
+           "nv": nv, "ne_directed": ne, "generation_and_load_s": gen_s, "steps": args.rmat26_steps,
+           "warmup": 3, "config": knobs, "autotune": _autotune_block(tuned),
+           "levels": {str(s): m["per_src"][s]["dirs"] for s in srcs[:4]},
+           "e2e": m["e2e"], "clocks": m["clocks"], "gpu_launches": m["launches"],
+           "roofline": {"bound": "hbm", "achieved": m["achieved"], "peak": peak, "unit": "GB/s",
+                        "frac": m["achieved"] / peak, "traffic": _captured_traffic("rmat26"),
+                        "kernel": "k_bfs_persistent", "peak_kind": peak_kind,
+                        "bytes_per_launch": m["bytes_per_launch"], "launch_ms": m["launch_ms"]},
+           "gteps": m["edges_total"] / m["t_total"] / 1e9,
+           "ms_per_traversal": m["traversal_ms_median"], "kernel_ms_median": m["kernel_ms_median"]}
+
+    def timed(fn, reps):
+        ts = []
+        for i in range(reps):
+            flush.fill_(i & 0xff)
+            a = torch.cuda.Event(enable_timing=True)
+            b = torch.cuda.Event(enable_timing=True)
+            a.record(stream)
+            fn()
+            b.record(stream)
+            torch.cuda.synchronize()
+            ts.append(a.elapsed_time(b))
+        return ts
+    # 64-lane multi-source BFS, knobs tuned on other sources
+    lanes = [int(x) for x in inputs.pick_sources(ro_h, 64, 5)]
+    mo = grx.opts()
+    mt = None
+    if not args.no_tune:
+        mt = autotune.tune_bfs_multi(g, ro_h, cache=args.tune_cache or autotune.DEFAULT_CACHE)
+        mo = grx.opts(alpha=mt["alpha"], beta=mt["beta"], push_bitmap=mt["push_bitmap"])
+    dm = torch.empty(64 * nv, dtype=torch.int32, device=f"cuda:{dev}")
+    grx.bfs_multi(g, lanes, depth_out=dm, opts=mo)
+    ms_edges = 0
+    for b in range(64):
+        ms_edges += int(deg_h[(dm[b * nv:(b + 1) * nv] >= 0).cpu().numpy()].sum())
+    ts = timed(lambda: grx.bfs_multi(g, lanes, depth_out=dm, opts=mo), 2)
+    so = grx.opts(collect_stats=1, alpha=mo.alpha, beta=mo.beta, push_bitmap=mo.push_bitmap)
+    grx.bfs_multi(g, lanes, depth_out=dm, opts=so)
+    mb = msbfs_bytes(grx.last_stats(g), nv, 8, 64)
+    grx.graph_status(g)
+    del dm
+    out["bfs_multi_64"] = {"ms": ts, "per_query_ms": statistics.median(ts) / 64,
+                           "gteps": ms_edges / (statistics.median(ts) / 1e3) / 1e9,
+                           "roofline_frac": mb / (statistics.median(ts) / 1e3) / 1e9 / peak,
+                           "knobs": None if mt is None else {k: mt[k] for k in ("alpha", "beta", "push_bitmap")},
+                           "one_by_one_per_query_ms": m["traversal_ms_median"]}
+    # PageRank, 20 iterations
+    r = torch.empty(nv, dtype=torch.float32, device=f"cuda:{dev}")
+    ts = timed(lambda: grx.pagerank(g, 0.85, 20, rank_out=r), 2)
+    grx.graph_status(g)
+    out["pagerank"] = {"ms": ts, "iters": 20, "ms_per_iter": statistics.median(ts) / 20,
+                       "roofline_frac": pr_bytes(nv, ne, 8, 20) / (statistics.median(ts) / 1e3) / 1e9 / peak}
+    del r
+    if with_cpu:
+        col_h = col.cpu().numpy()
+        e_cpu, s_cpu, used = run_oracle_bfs_sample(ro_h, col_h, srcs, args.cpu_budget26)
+        out["cpu_baseline"] = {"value": e_cpu / s_cpu / 1e9, "unit": "GTEPS", "cores": 1, "kind": "oracle",
+                               "sample": f"FIFO-queue BFS from {len(used)} of the {len(srcs)} seeded "
+                                         f"sources, single thread, {s_cpu:.1f} s"}
+        del col_h
+    grx.graph_free(g)
+    del g, ro, col
+    return out
+
+
+def serving_graphs(grx, torch, cfg, g, ro, col, w, ro_h):
+    """The serving set: resident R-MAT graphs of scales 18, 19, 20, 21, 22 and 24
+    (the workload's own graph stands in for its scale), weights U[1,64]; a
+    second handle (own workspace) of the two largest lets the traversal-
+    boundary server run two traversals of one graph at once."""
+    scales = (18, 19, 20, 21, 22, 24)
+    sgraphs, sdeg, sro, sreps = {}, {}, {}, {}
+    for sc in scales:
+        key = f"rmat{sc}"
+        if sc == cfg["scale"]:
+            sgraphs[key], sro[key] = g, ro_h
+            r2, c2, w2 = ro, col, w
+        else:
+            r2, c2, w2 = grx.rmat_graph_device(sc, 16, seed=sc, wmax=64, weight_seed=100 + sc)
+            sgraphs[key] = grx.graph_load_csr(r2, c2, w2, offsets64=sc >= 26)
+            sro[key] = r2.cpu().numpy()
+        if sc in scales[-2:]:
+            sreps[key] = [grx.graph_load_csr(r2, c2, w2, offsets64=sc >= 26)]
+    for k, h in sro.items():
+        sdeg[k] = torch.from_numpy(np.diff(h).astype(np.int32)).cuda()
+    torch.cuda.empty_cache()
+    return sgraphs, sdeg, sro, sreps
 
 
 def _loop_times(grx, torch, g, srcs, reps=3, **kw):
@@ -635,7 +780,7 @@ def grid_workload(args):
 
 
 def serving_bench(graphs: dict, degrees: dict, host_ro: dict, n_queries: int, seed: int = 7,
-                  loads=(0.5, 0.6, 0.7, 0.8, 1.0, 1.5, 2.0), replicas: dict | None = None) -> dict:
+                  loads=(0.5, 0.7, 0.8, 1.0, 1.5, 2.0), replicas: dict | None = None) -> dict:
     """Mixed BFS/SSSP queries with Poisson arrivals over resident graphs.
     mu = one-at-a-time saturation rate (all queries queued at once, after a
     warm-up pass); SLO = the one-at-a-time p99 at 0.5*mu; both batched
@@ -653,12 +798,15 @@ def serving_bench(graphs: dict, degrees: dict, host_ro: dict, n_queries: int, se
                                      serving.make_requests(spec, n_queries, 0.5 * mu, seed=seed + 1))
     slo = base["p99_ms"]
     points, tpoints = [], []
+    # one traversal-boundary server for every load point: calibrated batch
+    # sizes per graph and kind, workspaces allocated by a warm-up pass
+    tsrv = serving.TraversalServer(graphs, degrees, replicas=replicas, calibrate=True)
+    tsrv.run(serving.make_requests(spec, min(n_queries, 200), 0.0, seed=seed + 9), realtime=False)
     for f in loads:
         srv = serving.Server(graphs, degrees, steps_per_poll=2)
         st = srv.run(serving.make_requests(spec, n_queries, f * mu, seed=seed + 2))
         srv.close()
         points.append(dict(st, offered_qps=f * mu))
-        tsrv = serving.TraversalServer(graphs, degrees, replicas=replicas)
         st = tsrv.run(serving.make_requests(spec, n_queries, f * mu, seed=seed + 2))
         tpoints.append(dict(st, offered_qps=f * mu))
 
@@ -666,25 +814,30 @@ def serving_bench(graphs: dict, degrees: dict, host_ro: dict, n_queries: int, se
         ok = [p for p in pts if p["p99_ms"] <= slo]
         return max(ok, key=lambda p: p["gteps"]) if ok else None
     best, tbest = best_of(points), best_of(tpoints)
+
+    def compact(pts):          # (offered q/s, p50 ms, p99 ms, GTEPS, memory waits) per load point
+        return [[round(p["offered_qps"]), round(p["p50_ms"], 2), round(p["p99_ms"], 2), round(p["gteps"], 1),
+                 p.get("admission_waits", 0)] for p in pts]
     return {"graphs": {k: {"nv": g.nv, "ne": g.ne} for k, g in graphs.items()},
             "queries_per_point": n_queries, "mix": "50/50 BFS/SSSP, graph uniform, Poisson arrivals",
-            "one_at_a_time": {"saturation_qps": mu, "saturation_gteps": sat["gteps"],
-                              "at_half_saturation": base},
+            "one_at_a_time": {"saturation_qps": round(mu), "saturation_gteps": sat["gteps"],
+                              "p50_ms_at_half": base["p50_ms"], "p99_ms_at_half": base["p99_ms"]},
             "slo_p99_ms": slo,
+            "points_fields": ["offered_qps", "p50_ms", "p99_ms", "gteps", "admission_waits"],
+            "level_batched_points": compact(points),
+            "traversal_batched_points": compact(tpoints),
             "one_at_a_time_gteps_within_slo": base["gteps"],
-            "level_batched": {"points": points,
-                              "best_gteps_within_slo": best["gteps"] if best else None,
-                              "best_p50_ms": best["p50_ms"] if best else None,
-                              "best_p99_ms": best["p99_ms"] if best else None},
-            "traversal_batched": {"points": tpoints,
-                                  "best_gteps_within_slo": tbest["gteps"] if tbest else None,
-                                  "best_p50_ms": tbest["p50_ms"] if tbest else None,
-                                  "best_p99_ms": tbest["p99_ms"] if tbest else None}}
+            "level_batched_best_gteps_within_slo": best["gteps"] if best else None,
+            "traversal_batched_best_gteps_within_slo": tbest["gteps"] if tbest else None,
+            "traversal_batched_best_p50_p99_ms": [tbest["p50_ms"], tbest["p99_ms"]] if tbest else None,
+            "traversal_batch_sizes": {f"{k[0]}/{k[1]}": v for k, v in (tsrv.thresholds or {}).items()}}
 
 
-def other_primitives(grx, g, srcs, nv, ne, off_bytes, deg_h, flush, stream, peak, ro_h=None, col_dev=None):
+def other_primitives(grx, g, srcs, nv, ne, off_bytes, deg_h, flush, stream, peak, ro_h=None, col_dev=None,
+                     tune=True):
     """SSSP, CC, multi-source BFS/SSSP, PageRank and BC on the same resident
-    graph (CUDA events)."""
+    graph (CUDA events).  The multi-source BFS runs with its own tuned alpha /
+    beta / push_bitmap."""
     import torch
     out = {}
 
@@ -726,18 +879,25 @@ def other_primitives(grx, g, srcs, nv, ne, off_bytes, deg_h, flush, stream, peak
     # 64-lane multi-source BFS and batched SSSP (one launch each)
     from paper_1504_04804_gb300 import inputs
     lanes =[int(s) for s in inputs.pick_sources(np.concatenate([[0], np.cumsum(deg_h)]), 64, seed=11)]
+    mkw, mt = {}, None
+    if tune:
+        from paper_1504_04804_gb300 import autotune
+        mt = autotune.tune_bfs_multi(g, np.concatenate([[0], np.cumsum(deg_h)]))
+        mkw = {k: mt[k] for k in ("alpha", "beta", "push_bitmap")}
+    mo = grx.opts(**mkw)
     dm = torch.empty(64 * nv, dtype=torch.int32, device=flush.device)
-    grx.bfs_multi(g, lanes, depth_out=dm)
+    grx.bfs_multi(g, lanes, depth_out=dm, opts=mo)
     dmh = dm.view(64, nv).cpu().numpy()
     ms_edges = int(sum(int(deg_h[row >= 0].sum()) for row in dmh))
     ms_pairs = int((dmh >= 0).sum())
     del dmh
-    ts = timed(lambda i: grx.bfs_multi(g, lanes, depth_out=dm), 3)
-    grx.bfs_multi(g, lanes, depth_out=dm, opts=grx.opts(collect_stats=1))
+    ts = timed(lambda i: grx.bfs_multi(g, lanes, depth_out=dm, opts=mo), 3)
+    grx.bfs_multi(g, lanes, depth_out=dm, opts=grx.opts(collect_stats=1, **mkw))
     mb = msbfs_bytes(grx.last_stats(g), nv, off_bytes, 64)
     out["bfs_multi_64"] = {"ms": ts, "gteps": ms_edges / (statistics.median(ts) / 1e3) / 1e9,
                            "per_query_ms": statistics.median(ts) / 64,
-                           "roofline_frac": mb / (statistics.median(ts) / 1e3) / 1e9 / peak}
+                           "roofline_frac": mb / (statistics.median(ts) / 1e3) / 1e9 / peak,
+                           "knobs": mkw or None, "tuning_s": None if mt is None else mt["seconds"]}
     if g.weighted:
         dd = torch.empty(16 * nv, dtype=torch.int32, device=flush.device)
         ts = timed(lambda i: grx.sssp_multi(g, lanes[:16], dist_out=dd), 2)

@@ -343,6 +343,14 @@ grx_status grx_batch_poll(grx_batch *b, uint64_t *retired_mask_out);
 /* Device bytes a batch of `kind` on g needs (for admission by free memory). */
 grx_status grx_batch_footprint(const grx_graph *g, int kind, size_t *bytes_out);
 
+/* Device bytes the next bfs_multi (kind GRX_KIND_BFS) or sssp_multi
+ * (GRX_KIND_SSSP) call on g will allocate from the ctx allocator for its
+ * workspace -- 0 once a previous call allocated it; the caller's output
+ * array is not included.  For admission by free memory (the north-star
+ * serving loop; the paper sizes its buffers "just enough", Sec. 6.2).
+ * NULL argument or bad kind -> GRX_EINVAL. */
+grx_status grx_multi_footprint(const grx_graph *g, int kind, size_t *bytes_out);
+
 #ifdef __cplusplus
 }
 #endif

@@ -8,9 +8,16 @@ timings on a few seeded tuning sources:
 * the switch rule: the paper's estimate FV = |Q|*E/V, or the frontier's exact
   edge count (``exact_fv``), which the append counter provides for free;
 * alpha (push->pull) and beta (pull->push);
-* the persistent grid size (full occupancy or half of it), the load-balance
-  knob that remains at run time -- edge tiles are balanced by construction,
-  and the per-lane / per-group widths are compile-time constants;
+* the persistent grid size (full occupancy or half of it);
+* the load-balance threshold between the two push kinds (``push_bitmap``):
+  levels whose frontier holds at least push_bitmap * nv edges mark targets in
+  a bitmap and build the next queue in a second, word-owning pass; smaller
+  ones claim each target with an atomic and append it at once.  Searched
+  after the switch knobs (coordinate descent).  Edge tiles are balanced by
+  construction, and the per-lane / per-group widths are compile-time
+  constants;
+* for the 64-lane multi-source BFS, its own alpha / beta / push_bitmap
+  (``tune_bfs_multi``): the rule acts on lane popcounts there;
 * for SSSP, the near-far band width delta (``tune_sssp_delta``).
 
 Results do not depend on the parameters (the tests check this); only the
@@ -31,6 +38,10 @@ import numpy as np
 ALPHAS = (1e-6, 1e-5, 1e-4, 1e-3, 5e-3, 0.01, 0.05, 0.2)
 BETAS = (0.01, 0.1, 1.0)
 RULES = (0, 1)
+# push_bitmap candidates: 0 = the library default (1/8), < 0 = never
+PUSH_BITMAPS = (0.0, 1.0 / 64, 1.0 / 32, 0.5, -1.0)
+MULTI_ALPHAS = (1e-4, 1e-3, 0.01, 0.05, 0.2, 1.0)
+MULTI_BETAS = (0.01, 0.1, 1.0)
 DEFAULT_CACHE = os.path.join(os.path.expanduser("~"), ".cache", "grx_autotune.json")
 
 
@@ -82,8 +93,8 @@ def _time_config(grx, torch, g, sources, kw, reps):
 def tune_bfs(g, row_offsets, n_sources: int = 8, seed: int = 2, reps: int = 2,
              cache: str | None = DEFAULT_CACHE, force: bool = False) -> dict:
     """Search the knobs for direction-optimising BFS on a loaded graph.
-    Returns {"alpha", "beta", "exact_fv", "grid_blocks", "ms", "tried", "seconds",
-    "fingerprint", "cached"}."""
+    Returns {"alpha", "beta", "exact_fv", "grid_blocks", "push_bitmap", "ms",
+    "tried", "seconds", "fingerprint", "cached"}."""
     import torch
 
     from . import grx, inputs
@@ -110,11 +121,77 @@ def tune_bfs(g, row_offsets, n_sources: int = 8, seed: int = 2, reps: int = 2,
             best = (tot, kw, med)
         if full is None:
             full = _occupancy_grid(grx, g)
+    # then the push-kind threshold with the chosen switch knobs
+    base = dict(best[1])
+    for pb in PUSH_BITMAPS[1:]:
+        kw = dict(base, push_bitmap=pb)
+        med, tot = _time_config(grx, torch, g, sources, kw, reps)
+        tried += 1
+        if tot < best[0]:
+            best = (tot, kw, med)
     tot, kw, med = best
     grx.graph_status(g)
     res = {"alpha": kw["alpha"], "beta": kw["beta"], "exact_fv": kw["exact_fv"],
-           "grid_blocks": kw.get("grid_blocks", 0), "ms": med, "tried": tried,
+           "grid_blocks": kw.get("grid_blocks", 0), "push_bitmap": kw.get("push_bitmap", 0.0),
+           "ms": med, "tried": tried,
            "seconds": time.time() - t0, "fingerprint": fp, "tuning_sources": sources}
+    if cache:
+        data = _load(cache)
+        data[fp] = res
+        _save(cache, data)
+    return dict(res, cached=False)
+
+
+def tune_bfs_multi(g, row_offsets, lanes: int = 64, seed: int = 4, reps: int = 2,
+                   cache: str | None = DEFAULT_CACHE, force: bool = False) -> dict:
+    """alpha / beta (on lane popcounts) and then push_bitmap for the 64-lane
+    multi-source BFS, timed on one batch of `lanes` seeded tuning sources.
+    Returns {"alpha", "beta", "push_bitmap", "ms", "tried", "seconds",
+    "fingerprint", "cached"}."""
+    import torch
+
+    from . import grx, inputs
+    fp = fingerprint(row_offsets) + f"_multi{lanes}"
+    if cache and not force:
+        hit = _load(cache).get(fp)
+        if hit:
+            return dict(hit, cached=True)
+    t0 = time.time()
+    sources = [int(s) for s in inputs.pick_sources(row_offsets, lanes, seed)]
+    out = torch.empty(len(sources) * g.nv, dtype=torch.int32, device=f"cuda:{g.device}")
+    stream = torch.cuda.current_stream()
+
+    def timed(kw):
+        o = grx.opts(**kw)
+        grx.bfs_multi(g, sources, depth_out=out, opts=o)            # warm
+        ev0 = torch.cuda.Event(enable_timing=True)
+        ev1 = torch.cuda.Event(enable_timing=True)
+        ev0.record(stream)
+        for _ in range(reps):
+            grx.bfs_multi(g, sources, depth_out=out, opts=o)
+        ev1.record(stream)
+        ev1.synchronize()
+        return ev0.elapsed_time(ev1) / reps
+
+    best, tried = None, 0
+    for a, b in itertools.product(MULTI_ALPHAS, MULTI_BETAS):
+        kw = {"alpha": a, "beta": b}
+        ms = timed(kw)
+        tried += 1
+        if best is None or ms < best[0]:
+            best = (ms, kw)
+    base = dict(best[1])
+    for pb in PUSH_BITMAPS[1:]:
+        kw = dict(base, push_bitmap=pb)
+        ms = timed(kw)
+        tried += 1
+        if ms < best[0]:
+            best = (ms, kw)
+    ms, kw = best
+    grx.graph_status(g)
+    res = {"alpha": kw["alpha"], "beta": kw["beta"], "push_bitmap": kw.get("push_bitmap", 0.0),
+           "ms": ms, "tried": tried, "seconds": time.time() - t0, "fingerprint": fp,
+           "tuning_sources": sources}
     if cache:
         data = _load(cache)
         data[fp] = res
@@ -181,7 +258,7 @@ def _occupancy_grid(grx, g) -> int:
 
 def opts_from(grx, tuned: dict, **extra):
     """grx_opts carrying a tuning result."""
-    kw = {"alpha": tuned["alpha"], "beta": tuned["beta"], "exact_fv": tuned["exact_fv"],
-          "grid_blocks": tuned.get("grid_blocks", 0)}
+    kw = {"alpha": tuned["alpha"], "beta": tuned["beta"], "exact_fv": tuned.get("exact_fv", 0),
+          "grid_blocks": tuned.get("grid_blocks", 0), "push_bitmap": tuned.get("push_bitmap", 0.0)}
     kw.update(extra)
     return grx.opts(**kw)

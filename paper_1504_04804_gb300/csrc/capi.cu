@@ -353,6 +353,26 @@ grx_status grx_ensure_ms_workspace(grx_graph *g, cudaStream_t s) {
     return GRX_OK;
 }
 
+// Bytes grx_ensure_workspace / grx_ensure_ms_workspace would allocate now.
+static size_t workspace_new_bytes(const grx_graph *g, bool multi) {
+    const size_t nv = (size_t)g->nv, wb = (size_t)g->words * 4;
+    size_t b = 0;
+    if (!g->ws_ready)
+        b += wb + 3 * (wb + nv * 8 + nv * (g->off64 ? 8 : 4)) + 2 * nv * 4 + nv * sizeof(int2) +
+             sizeof(TravCtl) + sizeof(unsigned int) * GRX_MAX_GRID + sizeof(DevStats) + nv * 4;
+    if (multi && !g->ms_ready) b += 5 * nv * 8;
+    return b;
+}
+
+extern "C" grx_status grx_multi_footprint(const grx_graph *g, int kind, size_t *bytes_out) {
+    if (!g || !bytes_out) return grx_fail(GRX_EINVAL, "grx_multi_footprint: NULL argument");
+    if (kind != GRX_KIND_BFS && kind != GRX_KIND_SSSP)
+        return grx_fail(GRX_EINVAL, "grx_multi_footprint: bad kind %d", kind);
+    *bytes_out = workspace_new_bytes(g, true) +
+                 (kind == GRX_KIND_BFS ? grx_msbfs_new_bytes(g) : grx_mssp_new_bytes(g));
+    return GRX_OK;
+}
+
 extern "C" grx_status grx_graph_status(grx_graph *g, void *stream) {
     if (!g) return grx_fail(GRX_EINVAL, "grx_graph_status: NULL graph");
     cudaStream_t s = (cudaStream_t)stream;

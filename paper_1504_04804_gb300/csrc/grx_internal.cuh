@@ -168,6 +168,10 @@ grx_status grx_edge_tiles(grx_graph *g, int tile, cudaStream_t s, const int2 **o
 
 grx_status grx_msbfs_launch(grx_graph *g, const int32_t *srcs, int n, int32_t *depth,
                             const grx_opts *o, cudaStream_t s);
+// Device bytes the next multi-source BFS / batched SSSP launch allocates for
+// its own workspace on g (0 once allocated; shared pieces counted by both).
+size_t grx_msbfs_new_bytes(const grx_graph *g);
+size_t grx_mssp_new_bytes(const grx_graph *g);
 grx_status grx_mssp_launch(grx_graph *g, const int32_t *srcs, int n, uint32_t *dist,
                            const grx_opts *o, cudaStream_t s);
 

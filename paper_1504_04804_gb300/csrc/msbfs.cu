@@ -810,6 +810,19 @@ grx_status ms_launch_typed(grx_graph *g, const int32_t *srcs, int n, int32_t *de
 
 }  // namespace
 
+size_t grx_msbfs_new_bytes(const grx_graph *g) {
+    size_t b = 0;
+    const int64_t ntiles = (g->ne + MS_PTILE - 1) / MS_PTILE;
+    const size_t nt = (size_t)(ntiles > 0 ? ntiles : 1);
+    bool have_tiles = false;
+    for (int i = 0; i < (int)(sizeof g->etiles / sizeof g->etiles[0]); ++i)
+        if (g->etiles[i] && g->etile_size[i] == MS_PTILE) have_tiles = true;
+    if (ntiles > 0 && !have_tiles) b += nt * sizeof(int2);
+    if (!g->ms_fix) b += nt + nt * 4 + (size_t)MS_HSLOTS * (size_t)g->nv * 8;
+    if (!g->ms_tbits) b += (size_t)g->words * 4 + 16;
+    return b;
+}
+
 grx_status grx_msbfs_launch(grx_graph *g, const int32_t *srcs, int n, int32_t *depth,
                             const grx_opts *o, cudaStream_t s) {
     if (g->off64)

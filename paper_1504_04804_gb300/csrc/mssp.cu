@@ -423,6 +423,13 @@ grx_status mp_launch_typed(grx_graph *g, const int32_t *srcs, int n, uint32_t *d
 
 }  // namespace
 
+size_t grx_mssp_new_bytes(const grx_graph *g) {
+    size_t b = 0;
+    if (!g->ms_dist) b += (size_t)g->nv * 64 * sizeof(uint32_t);
+    if (!g->ms_tbits) b += (size_t)g->words * 4 + 16;
+    return b;
+}
+
 grx_status grx_mssp_launch(grx_graph *g, const int32_t *srcs, int n, uint32_t *dist,
                            const grx_opts *o, cudaStream_t s) {
     if (!g->ms_dist) {

@@ -90,6 +90,7 @@ SIGNATURES = [
     ("grx_batch_step", _I, [_P, _I]),
     ("grx_batch_poll", _I, [_P, _P]),
     ("grx_batch_footprint", _I, [_P, _I, _P]),
+    ("grx_multi_footprint", _I, [_P, _I, _P]),
     ("grx_rmat_edges", _I, [_I, _I64, _U64, _U64, _U64, _U64, _P, _P, _P]),
     ("grx_edge_weights", _I, [_I64, _I64, _P, _P, ctypes.c_uint32, _U64, _P, _P]),
     ("grx_grid_edges", _I, [_I64, _I64, _U64, _U64, _P, _P, _P, _P]),
@@ -419,6 +420,13 @@ GRX_KIND_BFS, GRX_KIND_SSSP = 0, 1
 def batch_footprint(g: Graph, kind: int) -> int:
     n = ctypes.c_size_t()
     _check(lib().grx_batch_footprint(g.handle, int(kind), ctypes.byref(n)), "grx_batch_footprint")
+    return int(n.value)
+
+
+def multi_footprint(g: Graph, kind: int) -> int:
+    """Workspace bytes the next bfs_multi / sssp_multi on g will allocate (0 once it has)."""
+    n = ctypes.c_size_t()
+    _check(lib().grx_multi_footprint(g.handle, int(kind), ctypes.byref(n)), "grx_multi_footprint")
     return int(n.value)
 
 

@@ -22,10 +22,15 @@ served FIFO by single-source calls on one stream of the same GPU.
 
 ``TraversalServer`` batches at traversal boundaries instead: requests that
 arrive while a traversal runs join the next multi-source traversal of their
-graph and kind (one persistent kernel for up to 64 lanes).
+graph and kind (one persistent kernel for up to 64 lanes).  It admits by free
+device memory too (``plan_lanes``): a traversal starts only when its
+workspace (``grx_multi_footprint``, allocated on a handle's first multi-source
+call) and its lanes' outputs fit; otherwise it waits for running traversals
+to return memory, or, when none runs, starts with as many lanes as fit.
 """
 from __future__ import annotations
 
+import statistics
 import time
 from dataclasses import dataclass, field
 
@@ -239,7 +244,42 @@ class Server:
         self.slots = []
 
 
-def plan_job(pending: dict, sssp_multi_min: int = 24, lanes: int = 64, busy=()):
+def plan_lanes(wanted: int, ws_bytes: int, lane_bytes: int, free_bytes: int,
+               others_running: bool) -> int:
+    """Pure memory admission of one traversal (host logic, testable without
+    a GPU): the lanes (queries) to start now out of `wanted`, given the
+    workspace the launch would allocate first and the bytes each lane's
+    output needs.  All of them when they fit; when they do not and other
+    traversals are running, 0 (wait: those return memory when they finish);
+    when nothing else runs, as many as fit, at least 1 -- and MemoryError if
+    not even one lane fits."""
+    if wanted <= 0:
+        return 0
+    if ws_bytes + wanted * lane_bytes <= free_bytes:
+        return wanted
+    if others_running:
+        return 0
+    fit = (free_bytes - ws_bytes) // lane_bytes if lane_bytes > 0 else wanted
+    if fit < 1:
+        raise MemoryError(f"a traversal needs {ws_bytes + lane_bytes} bytes of device memory, "
+                          f"{free_bytes} are free")
+    return int(min(wanted, fit))
+
+
+def batch_threshold(t_single_ms: float, t_batch_ms: dict) -> int:
+    """Smallest batch size n (a key of t_batch_ms: lanes -> measured time of
+    one n-lane traversal) from which sharing one traversal costs less than n
+    single-source traversals (per query, time / n < t_single); 65 (never
+    batch) when no measured size wins.  Host logic, testable without a GPU."""
+    wins = [n for n, t in sorted(t_batch_ms.items()) if n >= 2 and t < n * t_single_ms]
+    if not wins:
+        return 65
+    # from the smallest winning size on, assume larger batches win too
+    return wins[0]
+
+
+def plan_job(pending: dict, sssp_multi_min: int = 24, lanes: int = 64, busy=(), bfs_multi_min: int = 2,
+             thresholds: dict | None = None):
     """Pure policy of the traversal-boundary server (host logic, testable
     without a GPU).  pending: (graph, kind) -> requests in arrival order;
     busy: graphs with a traversal in flight (a graph's workspace serves one
@@ -247,14 +287,17 @@ def plan_job(pending: dict, sssp_multi_min: int = 24, lanes: int = 64, busy=()):
     served next: BFS requests (up to `lanes`) share one multi-source traversal
     when there are two or more, SSSP requests when at least `sssp_multi_min`
     wait (a batched SSSP lane costs less than a single-source traversal only
-    in a full batch); otherwise the oldest request runs alone.  Returns
+    in a full batch); `thresholds` ((graph, kind) -> batch size) overrides
+    both per graph; otherwise the oldest request runs alone.  Returns
     (key, requests, multi) or None when nothing can start."""
     keys = [k for k, v in pending.items() if v and k[0] not in busy]
     if not keys:
         return None
     key = min(keys, key=lambda k: (pending[k][0].arrival, pending[k][0].rid))
     waiting = pending[key]
-    thresh = 2 if key[1] == "bfs" else sssp_multi_min
+    thresh = bfs_multi_min if key[1] == "bfs" else sssp_multi_min
+    if thresholds and key in thresholds:
+        thresh = thresholds[key]
     if len(waiting) >= thresh:
         return key, waiting[:lanes], True
     return key, waiting[:1], False
@@ -271,15 +314,32 @@ class TraversalServer:
     traversals of different graphs (or of replica handles of one graph) run
     side by side, each on a share of the persistent grid while other work
     waits (a small graph's levels are as fast on a third of the SMs), on the
-    whole grid when it runs alone.  Each query's result is
-    its single-source result (tests check alone vs. in the mix)."""
+    whole grid when it runs alone.  A traversal starts only when its device
+    memory fits (``plan_lanes``: the handle's multi-source workspace on its
+    first use, plus per lane the output and the reduction's scratch).  Each
+    query's result is its single-source result (tests check alone vs. in the
+    mix)."""
 
     def __init__(self, graphs: dict, degrees: dict, sssp_multi_min: int = 24,
                  keep_results: bool = False, replicas: dict | None = None,
-                 share_big: int = 2, share_small: int = 4):
+                 share_big: int = 2, share_small: int = 4, reserve_bytes: int = 1 << 30,
+                 budget_bytes: int | None = None, calibrate: bool = False, sssp_share: int = 0,
+                 exclusive_ms: float | None = None):
         """replicas: graph name -> extra loaded handles of the same graph
         (each with its own workspace), so that several traversals of one
-        graph can be in flight."""
+        graph can be in flight.  budget_bytes caps the device memory the
+        server's traversals may take (default: what is free, less
+        reserve_bytes).  calibrate: time one single-source and one 8- and
+        64-lane traversal of each graph and kind at start-up and batch a kind
+        only from the size where sharing a traversal wins (batch_threshold);
+        otherwise BFS batches from 2 waiting requests and SSSP from
+        sssp_multi_min.  sssp_share > 0: an SSSP traversal that shares the
+        GPU runs on 1/sssp_share of the grid instead of its graph's share.
+        exclusive_ms (needs calibrate): a kind whose calibrated single-source
+        time is at least this long runs alone on the whole grid -- it starts
+        when nothing else runs and nothing starts beside it -- as in the
+        one-at-a-time baseline, so sharing never stretches the longest
+        queries, which set the tail latency; shorter kinds batch and share."""
         import torch
 
         from . import grx
@@ -298,6 +358,61 @@ class TraversalServer:
         big = max(g.ne for g in graphs.values())
         self.share = {name: max(1, full // (share_big if g.ne * 4 >= big else share_small))
                       for name, g in graphs.items()}
+        self.full = full
+        self.sssp_share = max(1, full // sssp_share) if sssp_share > 0 else 0
+        self.t_single = {}
+        self.thresholds = self._calibrate(graphs) if calibrate else None
+        self.exclusive = {k for k, t in self.t_single.items()
+                          if exclusive_ms is not None and t >= exclusive_ms}
+        self.reserve = reserve_bytes
+        self.budget = budget_bytes
+        self.used = 0                                 # bytes taken under budget_bytes
+        self.admission_waits = 0                      # traversals that waited for memory
+        self.shrunk = 0                               # traversals started with fewer lanes
+
+    def _calibrate(self, graphs: dict) -> dict:
+        """(graph, kind) -> batch size from which a shared traversal wins."""
+        from . import inputs
+        grx, torch = self.grx, self.torch
+        out = {}
+
+        def ms(fn):
+            fn()
+            a = torch.cuda.Event(enable_timing=True)
+            b = torch.cuda.Event(enable_timing=True)
+            a.record()
+            fn()
+            b.record()
+            b.synchronize()
+            return a.elapsed_time(b)
+        for name, g in graphs.items():
+            deg = self.degrees[name].cpu().numpy()
+            ro = np.concatenate([[0], np.cumsum(deg.astype(np.int64))])
+            srcs = [int(x) for x in inputs.pick_sources(ro, 64, seed=99)]
+            for kind in ("bfs", "sssp"):
+                if kind == "sssp" and not g.weighted:
+                    continue
+                one = grx.bfs if kind == "bfs" else grx.sssp
+                many = grx.bfs_multi if kind == "bfs" else grx.sssp_multi
+                t1 = statistics.median(ms(lambda s=s: one(g, s)) for s in srcs[:3])
+                self.t_single[(name, kind)] = t1
+                tb = {n: ms(lambda n=n: many(g, srcs[:n])) for n in (8, 64)}
+                out[(name, kind)] = batch_threshold(t1, tb)
+        torch.cuda.synchronize()
+        return out
+
+    def _free_bytes(self) -> int:
+        if self.budget is not None:
+            return self.budget - self.used
+        torch = self.torch
+        free, _ = torch.cuda.mem_get_info()
+        cached = torch.cuda.memory_reserved() - torch.cuda.memory_allocated()
+        return free + cached - self.reserve
+
+    def _lane_bytes(self, name: str) -> int:
+        # output (4 bytes per vertex), reached flags (1) and the masked degree
+        # the edge count reduces (4), per lane
+        return 9 * self.handles[name][0].nv + 64
 
     def _launch(self, slot, key, reqs, multi, grid_blocks):
         grx, torch = self.grx, self.torch
@@ -314,17 +429,21 @@ class TraversalServer:
                 out = grx.sssp_multi(g, srcs, opts=o, stream=st) if multi else \
                     grx.sssp(g, srcs[0], opts=o, stream=st).view(1, -1)
                 reached = out != -1                  # UINT32_MAX bits read as int32 -1
-            edges = (reached.to(torch.int64) * self.degrees[key[0]].to(torch.int64)).sum(dim=1)
+            edges = torch.where(reached, self.degrees[key[0]], 0).sum(dim=1, dtype=torch.int64)
+            del reached
             ev = torch.cuda.Event()
             ev.record(st)
         return out, edges, ev
 
     def run(self, requests: list[Request], realtime: bool = True) -> dict:
         torch = self.torch
+        self.admission_waits = 0
+        self.shrunk = 0
         order = sorted(requests, key=lambda r: r.arrival)
         pending: dict = {}
         nxt = 0
-        jobs: dict = {}                               # (graph, replica) -> (requests, out, edges, event)
+        jobs: dict = {}                               # (graph, replica) -> (requests, out, edges, event, bytes)
+        job_keys: dict = {}                           # (graph, replica) -> (graph, kind) of its traversal
         t0 = time.perf_counter()
         while nxt < len(order) or jobs or any(pending.values()):
             now = time.perf_counter() - t0
@@ -333,9 +452,11 @@ class TraversalServer:
                 pending.setdefault((r.graph, r.kind), []).append(r)
                 nxt += 1
             for slot in list(jobs):
-                reqs, out, edges, ev = jobs[slot]
+                reqs, out, edges, ev, nbytes = jobs[slot]
                 if not ev.query():
                     continue
+                self.used -= nbytes
+                job_keys.pop(slot, None)
                 done = time.perf_counter() - t0
                 e = edges.cpu().tolist()
                 # copies are made on the job's stream: its output memory goes back to
@@ -348,25 +469,50 @@ class TraversalServer:
                             r.result = out[i].clone()
                 del jobs[slot]
             while True:
+                if any(k in self.exclusive for k in job_keys.values()):
+                    break                             # an exclusive traversal runs alone
                 busy = {name for name, hs in self.handles.items()
                         if all((name, i) in jobs for i in range(len(hs)))}
-                plan = plan_job(pending, self.sssp_multi_min, busy=busy)
+                plan = plan_job(pending, self.sssp_multi_min, busy=busy, thresholds=self.thresholds)
                 if plan is None:
                     break
                 key, reqs, multi = plan
-                pending[key] = pending[key][len(reqs):]
+                if key in self.exclusive and jobs:
+                    break                             # waits until the GPU is free
                 slot = next((key[0], i) for i in range(len(self.handles[key[0]])) if (key[0], i) not in jobs)
+                g = self.handles[key[0]][slot[1]]
+                ws = self.grx.multi_footprint(g, KINDS[key[1]]) if multi else 0
+                lanes = plan_lanes(len(reqs), ws, self._lane_bytes(key[0]), self._free_bytes(),
+                                   others_running=bool(jobs))
+                if lanes == 0:                        # waits for memory from running traversals
+                    self.admission_waits += 1
+                    break
+                if lanes < len(reqs):
+                    self.shrunk += 1
+                    reqs = reqs[:lanes]
+                    multi = multi and lanes > 1
+                    ws = ws if multi else 0
+                pending[key] = pending[key][len(reqs):]
                 others = bool(jobs) or any(v for k, v in pending.items() if v and k != key)
                 for r in reqs:
                     r.admitted = now
-                out, edges, ev = self._launch(slot, key, reqs, multi, self.share[key[0]] if others else 0)
-                jobs[slot] = (reqs, out, edges, ev)
+                nbytes = len(reqs) * self._lane_bytes(key[0])
+                self.used += ws + nbytes               # the workspace stays with the handle
+                share = self.share[key[0]]
+                if key[1] == "sssp" and self.sssp_share:
+                    share = max(share, self.sssp_share)
+                if key in self.exclusive:
+                    others = False                    # alone: the whole grid
+                out, edges, ev = self._launch(slot, key, reqs, multi, share if others else 0)
+                jobs[slot] = (reqs, out, edges, ev, nbytes)
+                job_keys[slot] = key
             if not jobs and nxt < len(order) and realtime:
                 wait = order[nxt].arrival - (time.perf_counter() - t0)
                 if wait > 2e-4:
                     time.sleep(min(wait - 1e-4, 0.01))
         torch.cuda.synchronize()
-        return summarize(requests, time.perf_counter() - t0)
+        return dict(summarize(requests, time.perf_counter() - t0), admission_waits=self.admission_waits,
+                    shrunk=self.shrunk)
 
 
 def summarize(requests: list[Request], wall: float) -> dict:

@@ -30,14 +30,50 @@ def test_tuned_parameters_keep_results_exact(tmp_path):
     dg = grx.load(g)
     cache = os.path.join(tmp_path, "tune.json")
     t = autotune.tune_bfs(dg, g.row_offsets, cache=cache)
-    assert not t["cached"] and t["tried"] >= 36
+    assert not t["cached"] and t["tried"] >= 36 + len(autotune.PUSH_BITMAPS) - 1
     assert t["exact_fv"] in (0, 1) and t["alpha"] in autotune.ALPHAS and t["beta"] in autotune.BETAS
+    assert t["push_bitmap"] in autotune.PUSH_BITMAPS
     again = autotune.tune_bfs(dg, g.row_offsets, cache=cache)
     assert again["cached"] and again["alpha"] == t["alpha"]
     o = autotune.opts_from(grx, t)
     for s in inputs.pick_sources(g.row_offsets, 4, seed=5):
         assert np.array_equal(grx.bfs(dg, int(s), opts=o).cpu().numpy(),
                               oracle.bfs(g.row_offsets, g.col_indices, int(s)))
+    # every push_bitmap candidate gives the oracle's depths (the knob only moves work)
+    s = int(inputs.pick_sources(g.row_offsets, 1, seed=9)[0])
+    want = oracle.bfs(g.row_offsets, g.col_indices, s)
+    for pb in autotune.PUSH_BITMAPS:
+        for mode in (grx.GRX_DIR_AUTO, grx.GRX_DIR_PUSH):
+            o = grx.opts(push_bitmap=pb, direction=mode)
+            assert np.array_equal(grx.bfs(dg, s, opts=o).cpu().numpy(), want), (pb, mode)
+
+
+@pytest.mark.gpu
+def test_tuned_multi_source_knobs_keep_lanes_exact(tmp_path):
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_1504_04804_gb300 import build, grx
+    build.build()
+    g = inputs.rmat_graph(12, 16, seed=12)
+    dg = grx.load(g)
+    cache = os.path.join(tmp_path, "tune.json")
+    t = autotune.tune_bfs_multi(dg, g.row_offsets, lanes=16, cache=cache)
+    assert not t["cached"]
+    assert t["tried"] == len(autotune.MULTI_ALPHAS) * len(autotune.MULTI_BETAS) + len(autotune.PUSH_BITMAPS) - 1
+    assert t["alpha"] in autotune.MULTI_ALPHAS and t["beta"] in autotune.MULTI_BETAS
+    assert t["push_bitmap"] in autotune.PUSH_BITMAPS
+    assert autotune.tune_bfs_multi(dg, g.row_offsets, lanes=16, cache=cache)["cached"]
+    lanes = [int(x) for x in inputs.pick_sources(g.row_offsets, 16, seed=6)]
+    want = [oracle.bfs(g.row_offsets, g.col_indices, s) for s in lanes]
+    # the chosen knobs and every other candidate of the search keep every lane exact
+    cands = [dict(alpha=t["alpha"], beta=t["beta"], push_bitmap=t["push_bitmap"])]
+    cands += [dict(alpha=a, beta=b) for a in autotune.MULTI_ALPHAS for b in autotune.MULTI_BETAS]
+    cands += [dict(push_bitmap=pb) for pb in autotune.PUSH_BITMAPS]
+    for kw in cands:
+        d = grx.bfs_multi(dg, lanes, opts=grx.opts(**kw)).cpu().numpy()
+        for b in range(len(lanes)):
+            assert np.array_equal(d[b], want[b]), (kw, b)
 
 
 @pytest.mark.gpu

@@ -192,3 +192,79 @@ def test_plan_job_skips_graphs_with_a_traversal_in_flight():
     assert serving.plan_job(pend)[0] == ("a", "bfs")
     assert serving.plan_job(pend, busy={"a"})[0] == ("b", "bfs")
     assert serving.plan_job(pend, busy={"a", "b"}) is None
+
+
+def test_plan_lanes_admits_by_free_memory():
+    # everything fits
+    assert serving.plan_lanes(64, 1000, 10, 10**6, others_running=True) == 64
+    assert serving.plan_lanes(64, 1000, 10, 1000 + 640, others_running=False) == 64
+    # does not fit while others run: wait for their memory
+    assert serving.plan_lanes(64, 1000, 10, 1000 + 639, others_running=True) == 0
+    # nothing else runs: as many lanes as fit
+    assert serving.plan_lanes(64, 1000, 10, 1000 + 639, others_running=False) == 63
+    assert serving.plan_lanes(64, 0, 10, 15, others_running=False) == 1
+    assert serving.plan_lanes(0, 0, 10, 15, others_running=False) == 0
+    with pytest.raises(MemoryError):
+        serving.plan_lanes(64, 1000, 10, 1005, others_running=False)
+
+
+@pytest.mark.gpu
+def test_multi_footprint_matches_what_the_first_call_allocates(gpu):
+    torch, grx = gpu
+    hg = inputs.rmat_graph(13, 16, seed=13, wmax=64, weight_seed=113)
+    for kind, fn in ((grx.GRX_KIND_BFS, grx.bfs_multi), (grx.GRX_KIND_SSSP, grx.sssp_multi)):
+        g = grx.load(hg)
+        srcs = [int(s) for s in inputs.pick_sources(hg.row_offsets, 8, seed=2)]
+        out = torch.empty(8 * g.nv, dtype=torch.int32, device="cuda")
+        want = grx.multi_footprint(g, kind)
+        torch.cuda.synchronize()
+        before = torch.cuda.memory_allocated()
+        fn(g, srcs, out)
+        torch.cuda.synchronize()
+        got = torch.cuda.memory_allocated() - before
+        # torch's caching allocator rounds each block up to 512 bytes
+        assert want <= got <= want + 512 * 40, (kind, want, got)
+        assert grx.multi_footprint(g, kind) == 0
+        g.free()
+
+
+@pytest.mark.gpu
+def test_traversal_server_under_a_tiny_memory_budget(gpu):
+    """A budget that holds the workspace and only a few lanes' outputs: the
+    server starts smaller traversals (and waits for memory while one runs),
+    and every result is still the query's own single-source result."""
+    torch, grx = gpu
+    hg = {"r11": inputs.rmat_graph(11, 16, seed=11, wmax=64, weight_seed=111)}
+    graphs = {k: grx.load(v) for k, v in hg.items()}
+    degrees = {k: torch.from_numpy(np.diff(v.row_offsets).astype(np.int32)).cuda() for k, v in hg.items()}
+    g = graphs["r11"]
+    ws = max(grx.multi_footprint(g, grx.GRX_KIND_BFS), grx.multi_footprint(g, grx.GRX_KIND_SSSP))
+    lane = 9 * g.nv + 64
+    budget = grx.multi_footprint(g, grx.GRX_KIND_BFS) + grx.multi_footprint(g, grx.GRX_KIND_SSSP) + 6 * lane
+    reqs = serving.make_requests({k: (v.row_offsets, True) for k, v in hg.items()}, 120,
+                                 rate_qps=0.0, seed=8)
+    srv = serving.TraversalServer(graphs, degrees, sssp_multi_min=2, keep_results=True,
+                                  budget_bytes=budget)
+    stats = srv.run(reqs, realtime=False)
+    assert stats["queries"] == 120 and stats["shrunk"] > 0
+    assert srv.used <= budget and ws > 0
+    h = hg["r11"]
+    for r in reqs:
+        got = r.result.cpu().numpy()
+        if r.kind == "bfs":
+            assert np.array_equal(got, oracle.bfs(h.row_offsets, h.col_indices, r.src)), r
+        else:
+            assert np.array_equal(got.view(np.uint32),
+                                  oracle.sssp(h.row_offsets, h.col_indices, h.weights, r.src)), r
+
+
+def test_batch_threshold_from_measured_times():
+    # 8 lanes cost less than 8 single traversals: batch from 8
+    assert serving.batch_threshold(1.0, {8: 5.0, 64: 30.0}) == 8
+    # only the full batch wins
+    assert serving.batch_threshold(1.0, {8: 9.0, 64: 60.0}) == 64
+    # never wins: never batch
+    assert serving.batch_threshold(1.0, {8: 40.0, 64: 240.0}) == 65
+    pend = {("a", "sssp"): [serving.Request(i, "a", "sssp", 0, 0.1 * i) for i in range(10)]}
+    assert serving.plan_job(pend, thresholds={("a", "sssp"): 65})[2] is False
+    assert serving.plan_job(pend, thresholds={("a", "sssp"): 8})[2] is True
