@@ -338,7 +338,7 @@ def main():
     ap.add_argument("--cpu-budget", type=float, default=15.0,
                     help="seconds of oracle BFS for the cpu_baseline sample")
     ap.add_argument("--no-extra", action="store_true", help="skip SSSP/CC/PageRank timings")
-    ap.add_argument("--serving-queries", type=int, default=800,
+    ap.add_argument("--serving-queries", type=int, default=1600,
                     help="queries per offered-load point of the serving measurement")
     ap.add_argument("--no-tune", action="store_true",
                     help="use the paper's switch rule with --alpha/--beta instead of the autotuner")
@@ -780,13 +780,15 @@ def grid_workload(args):
 
 
 def serving_bench(graphs: dict, degrees: dict, host_ro: dict, n_queries: int, seed: int = 7,
-                  loads=(0.5, 0.7, 0.8, 1.0, 1.5, 2.0), replicas: dict | None = None) -> dict:
+                  loads=(0.5, 0.6, 0.7, 0.8, 1.0), level_loads=(0.5, 1.0), replicas: dict | None = None,
+                  max_batch_ms: float = 4.0) -> dict:
     """Mixed BFS/SSSP queries with Poisson arrivals over resident graphs.
     mu = one-at-a-time saturation rate (all queries queued at once, after a
-    warm-up pass); SLO = the one-at-a-time p99 at 0.5*mu; both batched
-    servers (lanes joining at level boundaries; at traversal boundaries) are
-    swept over offered loads (multiples of mu); reported: each system's best
-    GTEPS with p99 <= SLO."""
+    warm-up pass); SLO = the one-at-a-time p99 at 0.5*mu; the traversal-
+    boundary server and one-at-a-time are swept over the same offered loads
+    and arrivals (multiples of mu), the level-boundary server over
+    level_loads; reported: each system's best GTEPS with p99 <= SLO, and each
+    traversal-batched point's GTEPS over one-at-a-time's at the same p99."""
     from paper_1504_04804_gb300 import serving
     spec = {k: (host_ro[k], graphs[k].weighted) for k in graphs}
     serving.run_one_at_a_time(graphs, degrees, serving.make_requests(spec, min(n_queries, 200), 0.0,
@@ -797,18 +799,28 @@ def serving_bench(graphs: dict, degrees: dict, host_ro: dict, n_queries: int, se
     base = serving.run_one_at_a_time(graphs, degrees,
                                      serving.make_requests(spec, n_queries, 0.5 * mu, seed=seed + 1))
     slo = base["p99_ms"]
-    points, tpoints = [], []
-    # one traversal-boundary server for every load point: calibrated batch
-    # sizes per graph and kind, workspaces allocated by a warm-up pass
-    tsrv = serving.TraversalServer(graphs, degrees, replicas=replicas, calibrate=True)
-    tsrv.run(serving.make_requests(spec, min(n_queries, 200), 0.0, seed=seed + 9), realtime=False)
+    points, tpoints, bpoints = [], [], []
+    # one traversal-boundary server for every load point: batch sizes per
+    # graph and kind calibrated at start-up (a batch's traversal may add at
+    # most max_batch_ms), workspaces of every handle allocated by warm-up
+    # passes (all requests at once, then at the highest offered load)
+    tsrv = serving.TraversalServer(graphs, degrees, replicas=replicas, calibrate=True,
+                                   max_batch_ms=max_batch_ms)
+    tsrv.run(serving.make_requests(spec, min(n_queries, 400), 0.0, seed=seed + 9), realtime=False)
+    tsrv.run(serving.make_requests(spec, min(n_queries, 400), max(loads) * mu, seed=seed + 10))
     for f in loads:
-        srv = serving.Server(graphs, degrees, steps_per_poll=2)
-        st = srv.run(serving.make_requests(spec, n_queries, f * mu, seed=seed + 2))
-        srv.close()
-        points.append(dict(st, offered_qps=f * mu))
+        if f in level_loads:
+            srv = serving.Server(graphs, degrees, steps_per_poll=2)
+            st = srv.run(serving.make_requests(spec, n_queries, f * mu, seed=seed + 2))
+            srv.close()
+            points.append(dict(st, offered_qps=f * mu))
         st = tsrv.run(serving.make_requests(spec, n_queries, f * mu, seed=seed + 2))
         tpoints.append(dict(st, offered_qps=f * mu))
+        # one-at-a-time at the same load and arrivals: the curve equal-p99
+        # comparisons read off
+        st = serving.run_one_at_a_time(graphs, degrees, serving.make_requests(spec, n_queries, f * mu,
+                                                                              seed=seed + 2))
+        bpoints.append(dict(st, offered_qps=f * mu))
 
     def best_of(pts):
         ok = [p for p in pts if p["p99_ms"] <= slo]
@@ -826,11 +838,30 @@ def serving_bench(graphs: dict, degrees: dict, host_ro: dict, n_queries: int, se
             "points_fields": ["offered_qps", "p50_ms", "p99_ms", "gteps", "admission_waits"],
             "level_batched_points": compact(points),
             "traversal_batched_points": compact(tpoints),
+            "one_at_a_time_points": compact(bpoints),
+            "traversal_vs_one_at_a_time_gteps_at_equal_p99": equal_p99_ratios(tpoints, bpoints),
             "one_at_a_time_gteps_within_slo": base["gteps"],
             "level_batched_best_gteps_within_slo": best["gteps"] if best else None,
             "traversal_batched_best_gteps_within_slo": tbest["gteps"] if tbest else None,
             "traversal_batched_best_p50_p99_ms": [tbest["p50_ms"], tbest["p99_ms"]] if tbest else None,
             "traversal_batch_sizes": {f"{k[0]}/{k[1]}": v for k, v in (tsrv.thresholds or {}).items()}}
+
+
+def equal_p99_ratios(points, base_points):
+    """For each batched load point, its GTEPS over the one-at-a-time GTEPS
+    at the same p99, read off the baseline's (p99, GTEPS) curve by linear
+    interpolation (None outside the baseline's measured p99 range)."""
+    curve = sorted((p["p99_ms"], p["gteps"]) for p in base_points)
+    out = []
+    for p in points:
+        x = p["p99_ms"]
+        val = None
+        for (x0, y0), (x1, y1) in zip(curve, curve[1:]):
+            if x0 <= x <= x1 and x1 > x0:
+                val = y0 + (y1 - y0) * (x - x0) / (x1 - x0)
+                break
+        out.append(None if val is None else round(p["gteps"] / val, 3))
+    return out
 
 
 def other_primitives(grx, g, srcs, nv, ne, off_bytes, deg_h, flush, stream, peak, ro_h=None, col_dev=None,

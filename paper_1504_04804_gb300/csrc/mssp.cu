@@ -70,8 +70,10 @@ template <typename OffT>
 __device__ void mp_init_fill(const MpArgs<OffT> &a) {
     const int64_t tid = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
     const int64_t stride = (int64_t)gridDim.x * blockDim.x;
-    const int64_t total = (int64_t)a.nv * 64;
-    for (int64_t i = tid; i < total; i += stride) a.D[i] = 0xffffffffu;
+    // only the batch's lanes (rounded up to a 32-byte sector) are ever read
+    const int nl = (a.n + 7) & ~7;
+    const int64_t total = (int64_t)a.nv * nl;
+    for (int64_t i = tid; i < total; i += stride) a.D[(i / nl) * 64 + (i % nl)] = 0xffffffffu;
     for (int64_t v = tid; v < a.nv; v += stride) {
         a.next[v] = 0ull;
         a.cur[0][v] = 0ull;
@@ -108,6 +110,151 @@ __device__ void mp_seed(const MpArgs<OffT> &a) {
 }  // namespace
 
 namespace {
+
+// Relaxes a staged tile of `len` edges for every lane of the batch: one edge
+// at a time across the warp, thread = lane b (and b + 32 with two halves).
+// Improved lanes go to next[v] (and the touched bitmap in reduction rounds,
+// or the tile's touched list tbuf / nt otherwise).
+template <typename OffT>
+__device__ __forceinline__ void relax_lanes(const MpArgs<OffT> &a, MpWarpSmem<OffT> &w, int len, bool bmp,
+                                            int32_t *tbuf, int &nt, int halves) {
+    const unsigned int lane = threadIdx.x & 31;
+        for (int eb = 0; eb < len; eb += MP_UNROLL) {
+        int32_t vv[MP_UNROLL], uu[MP_UNROLL];
+        uint32_t ww[MP_UNROLL];
+        unsigned long long mm[MP_UNROLL];
+#pragma unroll
+        for (int k = 0; k < MP_UNROLL; ++k) {
+            const bool ok = eb + k < len;
+            const int j = ok ? w.er[eb + k] : 0;
+            vv[k] = ok ? w.ev[eb + k] : 0;
+            ww[k] = ok ? w.ew[eb + k] : 0u;
+            uu[k] = ok ? w.u[j] : 0;
+            mm[k] = ok ? w.cm[j] : 0ull;
+        }
+        unsigned long long imp[MP_UNROLL];
+#pragma unroll
+        for (int k = 0; k < MP_UNROLL; ++k) imp[k] = 0ull;
+        for (int h = 0; h < halves; ++h) {
+            const int b = (int)lane + 32 * h;
+            uint32_t du[MP_UNROLL], dv[MP_UNROLL];
+#pragma unroll
+            for (int k = 0; k < MP_UNROLL; ++k) {
+                const bool act = (mm[k] >> b) & 1ull;
+                du[k] = act ? __ldcg(a.D + (int64_t)uu[k] * 64 + b) : 0xffffffffu;
+                dv[k] = act ? __ldcg(a.D + (int64_t)vv[k] * 64 + b) : 0u;
+            }
+#pragma unroll
+            for (int k = 0; k < MP_UNROLL; ++k) {
+                bool improved = false;
+                if (du[k] != 0xffffffffu) {
+                    const uint64_t nd = (uint64_t)du[k] + ww[k];
+                    if (nd >= 0xffffffffull) {
+                        grx_set_status(a.ctl, GRX_ERANGE);
+                    } else if ((uint32_t)nd < dv[k]) {
+                        if (bmp) {
+                            // a reduction: the lane improves in this round,
+                            // by this proposal or a smaller one
+                            atomicMin(a.D + (int64_t)vv[k] * 64 + b, (uint32_t)nd);
+                            improved = true;
+                        } else {
+                            const uint32_t old = atomicMin(a.D + (int64_t)vv[k] * 64 + b, (uint32_t)nd);
+                            improved = (uint32_t)nd < old;
+                        }
+                    }
+                }
+                imp[k] |= (unsigned long long)__ballot_sync(GRX_FULL_MASK, improved) << (32 * h);
+            }
+        }
+        if (bmp) {
+#pragma unroll
+            for (int k = 0; k < MP_UNROLL; ++k) {
+                if (lane == (unsigned)k && imp[k]) {
+                    atomicOr(a.next + vv[k], imp[k]);                // results unused: reductions
+                    atomicOr(a.tbits + (vv[k] >> 5), 1u << (vv[k] & 31));
+                }
+            }
+        } else {
+#pragma unroll
+            for (int k = 0; k < MP_UNROLL; ++k) {
+                bool first = false;
+                if (lane == (unsigned)k && imp[k]) first = atomicOr(a.next + vv[k], imp[k]) == 0ull;
+                const unsigned int fm = __ballot_sync(GRX_FULL_MASK, first);
+                if (first) tbuf[nt + __popc(fm & lanemask_lt())] = vv[k];
+                nt += __popc(fm);
+            }
+        }
+    }
+}
+
+// The same for batches of at most G lanes (G = 8 or 16): the warp splits into
+// 32 / G groups and each group relaxes its own edge, thread = lane b of its
+// group's edge, so one warp instruction serves 32 / G edges.
+template <typename OffT, int G>
+__device__ __forceinline__ void relax_groups(const MpArgs<OffT> &a, MpWarpSmem<OffT> &w, int len, bool bmp,
+                                             int32_t *tbuf, int &nt) {
+    static_assert(G == 8 || G == 16, "lane groups of 8 or 16");
+    constexpr int EPW = 32 / G;                   // edges per warp instruction
+    const unsigned int lane = threadIdx.x & 31;
+    const int gi = (int)lane / G;                 // the thread's edge within a step
+    const int b = (int)lane % G;                  // its SSSP lane
+    const unsigned int gmask = (1u << G) - 1u;
+    for (int eb = 0; eb < len; eb += MP_UNROLL * EPW) {
+        int32_t vv[MP_UNROLL], uu[MP_UNROLL];
+        uint32_t ww[MP_UNROLL];
+        bool act[MP_UNROLL];
+#pragma unroll
+        for (int k = 0; k < MP_UNROLL; ++k) {
+            const int e = eb + k * EPW + gi;
+            const bool ok = e < len;
+            const int j = ok ? w.er[e] : 0;
+            vv[k] = ok ? w.ev[e] : 0;
+            ww[k] = ok ? w.ew[e] : 0u;
+            uu[k] = ok ? w.u[j] : 0;
+            act[k] = ok && ((w.cm[j] >> b) & 1ull);
+        }
+        uint32_t du[MP_UNROLL], dv[MP_UNROLL];
+#pragma unroll
+        for (int k = 0; k < MP_UNROLL; ++k) {
+            du[k] = act[k] ? __ldcg(a.D + (int64_t)uu[k] * 64 + b) : 0xffffffffu;
+            dv[k] = act[k] ? __ldcg(a.D + (int64_t)vv[k] * 64 + b) : 0u;
+        }
+#pragma unroll
+        for (int k = 0; k < MP_UNROLL; ++k) {
+            bool improved = false;
+            if (du[k] != 0xffffffffu) {
+                const uint64_t nd = (uint64_t)du[k] + ww[k];
+                if (nd >= 0xffffffffull) {
+                    grx_set_status(a.ctl, GRX_ERANGE);
+                } else if ((uint32_t)nd < dv[k]) {
+                    if (bmp) {
+                        atomicMin(a.D + (int64_t)vv[k] * 64 + b, (uint32_t)nd);
+                        improved = true;
+                    } else {
+                        const uint32_t old = atomicMin(a.D + (int64_t)vv[k] * 64 + b, (uint32_t)nd);
+                        improved = (uint32_t)nd < old;
+                    }
+                }
+            }
+            // the group's improved lanes; its first thread publishes them
+            const unsigned int imp = (__ballot_sync(GRX_FULL_MASK, improved) >> (gi * G)) & gmask;
+            bool first = false;
+            if (b == 0 && imp) {
+                if (bmp) {
+                    atomicOr(a.next + vv[k], (unsigned long long)imp);        // results unused: reductions
+                    atomicOr(a.tbits + (vv[k] >> 5), 1u << (vv[k] & 31));
+                } else {
+                    first = atomicOr(a.next + vv[k], (unsigned long long)imp) == 0ull;
+                }
+            }
+            if (!bmp) {
+                const unsigned int fm = __ballot_sync(GRX_FULL_MASK, first);
+                if (first) tbuf[nt + __popc(fm & lanemask_lt())] = vv[k];
+                nt += __popc(fm);
+            }
+        }
+    }
+}
 
 template <typename OffT>
 __device__ void mp_expand(const MpArgs<OffT> &a, int L, uint32_t q, uint64_t T, MpWarpSmem<OffT> &w,
@@ -169,72 +316,9 @@ __device__ void mp_expand(const MpArgs<OffT> &a, int L, uint32_t q, uint64_t T, 
         __syncwarp();
         const int len = (int)(e1 - (uint32_t)e0);
         int nt = 0;                                   // touched vertices of this tile (list rounds)
-        for (int eb = 0; eb < len; eb += MP_UNROLL) {
-            int32_t vv[MP_UNROLL], uu[MP_UNROLL];
-            uint32_t ww[MP_UNROLL];
-            unsigned long long mm[MP_UNROLL];
-#pragma unroll
-            for (int k = 0; k < MP_UNROLL; ++k) {
-                const bool ok = eb + k < len;
-                const int j = ok ? w.er[eb + k] : 0;
-                vv[k] = ok ? w.ev[eb + k] : 0;
-                ww[k] = ok ? w.ew[eb + k] : 0u;
-                uu[k] = ok ? w.u[j] : 0;
-                mm[k] = ok ? w.cm[j] : 0ull;
-            }
-            unsigned long long imp[MP_UNROLL];
-#pragma unroll
-            for (int k = 0; k < MP_UNROLL; ++k) imp[k] = 0ull;
-            for (int h = 0; h < halves; ++h) {
-                const int b = (int)lane + 32 * h;
-                uint32_t du[MP_UNROLL], dv[MP_UNROLL];
-#pragma unroll
-                for (int k = 0; k < MP_UNROLL; ++k) {
-                    const bool act = (mm[k] >> b) & 1ull;
-                    du[k] = act ? __ldcg(a.D + (int64_t)uu[k] * 64 + b) : 0xffffffffu;
-                    dv[k] = act ? __ldcg(a.D + (int64_t)vv[k] * 64 + b) : 0u;
-                }
-#pragma unroll
-                for (int k = 0; k < MP_UNROLL; ++k) {
-                    bool improved = false;
-                    if (du[k] != 0xffffffffu) {
-                        const uint64_t nd = (uint64_t)du[k] + ww[k];
-                        if (nd >= 0xffffffffull) {
-                            grx_set_status(a.ctl, GRX_ERANGE);
-                        } else if ((uint32_t)nd < dv[k]) {
-                            if (bmp) {
-                                // a reduction: the lane improves in this round,
-                                // by this proposal or a smaller one
-                                atomicMin(a.D + (int64_t)vv[k] * 64 + b, (uint32_t)nd);
-                                improved = true;
-                            } else {
-                                const uint32_t old = atomicMin(a.D + (int64_t)vv[k] * 64 + b, (uint32_t)nd);
-                                improved = (uint32_t)nd < old;
-                            }
-                        }
-                    }
-                    imp[k] |= (unsigned long long)__ballot_sync(GRX_FULL_MASK, improved) << (32 * h);
-                }
-            }
-            if (bmp) {
-#pragma unroll
-                for (int k = 0; k < MP_UNROLL; ++k) {
-                    if (lane == (unsigned)k && imp[k]) {
-                        atomicOr(a.next + vv[k], imp[k]);                // results unused: reductions
-                        atomicOr(a.tbits + (vv[k] >> 5), 1u << (vv[k] & 31));
-                    }
-                }
-            } else {
-#pragma unroll
-                for (int k = 0; k < MP_UNROLL; ++k) {
-                    bool first = false;
-                    if (lane == (unsigned)k && imp[k]) first = atomicOr(a.next + vv[k], imp[k]) == 0ull;
-                    const unsigned int fm = __ballot_sync(GRX_FULL_MASK, first);
-                    if (first) tbuf[nt + __popc(fm & lanemask_lt())] = vv[k];
-                    nt += __popc(fm);
-                }
-            }
-        }
+        if (a.n <= 8) relax_groups<OffT, 8>(a, w, len, bmp, tbuf, nt);
+        else if (a.n <= 16) relax_groups<OffT, 16>(a, w, len, bmp, tbuf, nt);
+        else relax_lanes<OffT>(a, w, len, bmp, tbuf, nt, halves);
         __syncwarp();
         // one append of the tile's touched vertices
         unsigned int base = 0;
@@ -306,7 +390,7 @@ __device__ void mp_finalize(const MpArgs<OffT> &a, int L, bool bmp, uint16_t *li
 namespace {
 
 template <typename OffT>
-__global__ void __launch_bounds__(MP_BLOCK, 2) k_mssp_persistent(MpArgs<OffT> a) {
+__global__ void __launch_bounds__(MP_BLOCK, 3) k_mssp_persistent(MpArgs<OffT> a) {
     __shared__ MpWarpSmem<OffT> wsm[MP_WARPS];
     __shared__ int32_t tbufs[MP_WARPS][MP_WTILE];
     __shared__ uint16_t lists[MP_WARPS][32 * 32];

@@ -266,16 +266,22 @@ def plan_lanes(wanted: int, ws_bytes: int, lane_bytes: int, free_bytes: int,
     return int(min(wanted, fit))
 
 
-def batch_threshold(t_single_ms: float, t_batch_ms: dict) -> int:
-    """Smallest batch size n (a key of t_batch_ms: lanes -> measured time of
-    one n-lane traversal) from which sharing one traversal costs less than n
-    single-source traversals (per query, time / n < t_single); 65 (never
-    batch) when no measured size wins.  Host logic, testable without a GPU."""
-    wins = [n for n, t in sorted(t_batch_ms.items()) if n >= 2 and t < n * t_single_ms]
+def batch_threshold(t_single_ms: float, t_batch_ms: dict, max_ms: float | None = None):
+    """Batch sizes worth serving from measured times (t_batch_ms: lanes ->
+    time of one traversal of that many lanes): (smallest n from which
+    sharing one traversal costs less than n single-source traversals, i.e.
+    time / n < t_single; the most lanes whose traversal stays within max_ms,
+    the latency a batch may add -- read off the measured sizes, at least the
+    smallest winning one).  (65, 64) -- never batch -- when no measured size
+    wins within max_ms.  Host logic, testable without a GPU."""
+    wins = [n for n, t in sorted(t_batch_ms.items())
+            if n >= 2 and t < n * t_single_ms and (max_ms is None or t <= max_ms)]
     if not wins:
-        return 65
-    # from the smallest winning size on, assume larger batches win too
-    return wins[0]
+        return 65, 64
+    # from the smallest winning size on, assume larger batches win too; the
+    # lane cap is the largest measured size within the latency bound
+    ok = [n for n, t in sorted(t_batch_ms.items()) if max_ms is None or t <= max_ms]
+    return wins[0], max(max(ok), wins[0])
 
 
 def plan_job(pending: dict, sssp_multi_min: int = 24, lanes: int = 64, busy=(), bfs_multi_min: int = 2,
@@ -287,8 +293,8 @@ def plan_job(pending: dict, sssp_multi_min: int = 24, lanes: int = 64, busy=(), 
     served next: BFS requests (up to `lanes`) share one multi-source traversal
     when there are two or more, SSSP requests when at least `sssp_multi_min`
     wait (a batched SSSP lane costs less than a single-source traversal only
-    in a full batch); `thresholds` ((graph, kind) -> batch size) overrides
-    both per graph; otherwise the oldest request runs alone.  Returns
+    in a full batch); `thresholds` ((graph, kind) -> (smallest, largest
+    batch)) overrides both per graph; otherwise the oldest request runs alone.  Returns
     (key, requests, multi) or None when nothing can start."""
     keys = [k for k, v in pending.items() if v and k[0] not in busy]
     if not keys:
@@ -297,7 +303,7 @@ def plan_job(pending: dict, sssp_multi_min: int = 24, lanes: int = 64, busy=(), 
     waiting = pending[key]
     thresh = bfs_multi_min if key[1] == "bfs" else sssp_multi_min
     if thresholds and key in thresholds:
-        thresh = thresholds[key]
+        thresh, lanes = thresholds[key]
     if len(waiting) >= thresh:
         return key, waiting[:lanes], True
     return key, waiting[:1], False
@@ -324,7 +330,8 @@ class TraversalServer:
                  keep_results: bool = False, replicas: dict | None = None,
                  share_big: int = 2, share_small: int = 4, reserve_bytes: int = 1 << 30,
                  budget_bytes: int | None = None, calibrate: bool = False, sssp_share: int = 0,
-                 exclusive_ms: float | None = None):
+                 exclusive_ms: float | None = None, max_batch_ms: float | None = None,
+                 full_grid_ms: float | None = None):
         """replicas: graph name -> extra loaded handles of the same graph
         (each with its own workspace), so that several traversals of one
         graph can be in flight.  budget_bytes caps the device memory the
@@ -339,7 +346,12 @@ class TraversalServer:
         time is at least this long runs alone on the whole grid -- it starts
         when nothing else runs and nothing starts beside it -- as in the
         one-at-a-time baseline, so sharing never stretches the longest
-        queries, which set the tail latency; shorter kinds batch and share."""
+        queries, which set the tail latency; shorter kinds batch and share.
+        max_batch_ms (with calibrate): a batch's traversal may take at most
+        this long (the latency batching may add to its queries).
+        full_grid_ms (with calibrate): kinds whose single-source time is at
+        least this long start on the whole grid at once, beside whatever runs
+        (their blocks take SMs as they free up); the rest use shares."""
         import torch
 
         from . import grx
@@ -361,9 +373,12 @@ class TraversalServer:
         self.full = full
         self.sssp_share = max(1, full // sssp_share) if sssp_share > 0 else 0
         self.t_single = {}
+        self.max_batch_ms = max_batch_ms
         self.thresholds = self._calibrate(graphs) if calibrate else None
         self.exclusive = {k for k, t in self.t_single.items()
                           if exclusive_ms is not None and t >= exclusive_ms}
+        self.full_grid = {k for k, t in self.t_single.items()
+                          if full_grid_ms is not None and t >= full_grid_ms}
         self.reserve = reserve_bytes
         self.budget = budget_bytes
         self.used = 0                                 # bytes taken under budget_bytes
@@ -371,7 +386,7 @@ class TraversalServer:
         self.shrunk = 0                               # traversals started with fewer lanes
 
     def _calibrate(self, graphs: dict) -> dict:
-        """(graph, kind) -> batch size from which a shared traversal wins."""
+        """(graph, kind) -> (smallest, largest) batch worth a shared traversal."""
         from . import inputs
         grx, torch = self.grx, self.torch
         out = {}
@@ -396,8 +411,8 @@ class TraversalServer:
                 many = grx.bfs_multi if kind == "bfs" else grx.sssp_multi
                 t1 = statistics.median(ms(lambda s=s: one(g, s)) for s in srcs[:3])
                 self.t_single[(name, kind)] = t1
-                tb = {n: ms(lambda n=n: many(g, srcs[:n])) for n in (8, 64)}
-                out[(name, kind)] = batch_threshold(t1, tb)
+                tb = {n: ms(lambda n=n: many(g, srcs[:n])) for n in (4, 8, 16, 32, 64)}
+                out[(name, kind)] = batch_threshold(t1, tb, self.max_batch_ms)
         torch.cuda.synchronize()
         return out
 
@@ -501,8 +516,8 @@ class TraversalServer:
                 share = self.share[key[0]]
                 if key[1] == "sssp" and self.sssp_share:
                     share = max(share, self.sssp_share)
-                if key in self.exclusive:
-                    others = False                    # alone: the whole grid
+                if key in self.exclusive or key in self.full_grid:
+                    others = False                    # the whole grid
                 out, edges, ev = self._launch(slot, key, reqs, multi, share if others else 0)
                 jobs[slot] = (reqs, out, edges, ev, nbytes)
                 job_keys[slot] = key

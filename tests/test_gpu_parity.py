@@ -344,10 +344,11 @@ def test_bfs_multi_few_lanes_and_stats(grx, loaded):
 
 @pytest.mark.parametrize("name", ["rmat10", "rmat13", "rmat14_ef4", "grid64", "path", "star", "disconnected"])
 @pytest.mark.parametrize("pb", list(PUSH_BITMAP))
-def test_sssp_multi_lanes_match_oracle(grx, loaded, name, pb):
+@pytest.mark.parametrize("nl", [5, 8, 13, 16, 42])      # lane groups of 8, of 16, one lane per thread
+def test_sssp_multi_lanes_match_oracle(grx, loaded, name, pb, nl):
     g, dg = GRAPHS[name], loaded[name]
     srcs = _sources(g, 40, seed=3) if name != "disconnected" else [1, 5, 10, 30, 0]
-    srcs = srcs + [srcs[0], g.nv - 1]
+    srcs = (srcs + [srcs[0], g.nv - 1] + srcs)[:nl]
     d = grx.sssp_multi(dg, srcs, opts=grx.opts(push_bitmap=PUSH_BITMAP[pb])).cpu().numpy().view(np.uint32)
     grx.graph_status(dg)
     for b, s in enumerate(srcs):

@@ -259,12 +259,16 @@ def test_traversal_server_under_a_tiny_memory_budget(gpu):
 
 
 def test_batch_threshold_from_measured_times():
-    # 8 lanes cost less than 8 single traversals: batch from 8
-    assert serving.batch_threshold(1.0, {8: 5.0, 64: 30.0}) == 8
+    # 8 lanes cost less than 8 single traversals: batch from 8, up to 64
+    assert serving.batch_threshold(1.0, {8: 5.0, 64: 30.0}) == (8, 64)
     # only the full batch wins
-    assert serving.batch_threshold(1.0, {8: 9.0, 64: 60.0}) == 64
+    assert serving.batch_threshold(1.0, {8: 9.0, 64: 60.0}) == (64, 64)
     # never wins: never batch
-    assert serving.batch_threshold(1.0, {8: 40.0, 64: 240.0}) == 65
-    pend = {("a", "sssp"): [serving.Request(i, "a", "sssp", 0, 0.1 * i) for i in range(10)]}
-    assert serving.plan_job(pend, thresholds={("a", "sssp"): 65})[2] is False
-    assert serving.plan_job(pend, thresholds={("a", "sssp"): 8})[2] is True
+    assert serving.batch_threshold(1.0, {8: 40.0, 64: 240.0}) == (65, 64)
+    # a latency bound: batches of up to 16 lanes take at most 12 ms
+    assert serving.batch_threshold(1.0, {8: 5.0, 16: 9.0, 64: 30.0}, max_ms=12.0) == (8, 16)
+    assert serving.batch_threshold(1.0, {8: 5.0, 64: 30.0}, max_ms=4.0) == (65, 64)
+    pend = {("a", "sssp"): [serving.Request(i, "a", "sssp", 0, 0.1 * i) for i in range(20)]}
+    assert serving.plan_job(pend, thresholds={("a", "sssp"): (65, 64)})[2] is False
+    key, reqs, multi = serving.plan_job(pend, thresholds={("a", "sssp"): (8, 16)})
+    assert multi and len(reqs) == 16
