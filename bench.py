@@ -394,6 +394,9 @@ def main():
     if not args.no_extra:
         extra = other_primitives(grx, g, srcs, nv, ne, off_bytes, deg_h, flush, stream, peak,
                                  ro_h=ro_h, col_dev=col, tune=not args.no_tune)
+        extra["bfs64"] = bfs64_leg(grx, torch, ro, col, srcs,
+                                   sum(m["per_src"][s]["edges"] for s in srcs), knobs, flush, stream,
+                                   m["traversal_ms_median"])
     if not args.no_extra and args.serving_queries > 0:
         sgraphs, sdeg, sro, sreps = serving_graphs(grx, torch, cfg, g, ro, col, w, ro_h)
         try:
@@ -562,6 +565,33 @@ def measure_bfs(grx, torch, g, ro_h, srcs, knobs, steps, warmup, off_bytes, flus
                     "d2h_bytes_per_step": 4 * nv * len(srcs)}}
 
 
+def bfs64_leg(grx, torch, ro, col, srcs, edges, knobs, flush, stream, t32_ms):
+    """The same traversals on the graph loaded with 64-bit vertex ids
+    (graph_load_csr64, bfs64): per-traversal device time, GTEPS and the ratio
+    to the 32-bit path (Sec. 7 / Table 5 report about 0.5x)."""
+    g64 = grx.graph_load_csr64(ro.to(torch.int64), col.to(torch.int64))
+    o = grx.opts(alpha=knobs["alpha"], beta=knobs["beta"], exact_fv=knobs["exact_fv"])
+    depth = torch.empty(g64.nv, dtype=torch.int32, device=ro.device)
+    for s in srcs[:2]:
+        grx.bfs64(g64, s, depth_out=depth, opts=o)
+    ts = []
+    for i, s in enumerate(srcs):
+        flush.fill_(i & 0xff)
+        a = torch.cuda.Event(enable_timing=True)
+        b = torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        grx.bfs64(g64, s, depth_out=depth, opts=o)
+        b.record(stream)
+        b.synchronize()
+        ts.append(a.elapsed_time(b))
+    grx.graph_status(g64)
+    g64.free()
+    del g64, depth
+    torch.cuda.empty_cache()
+    return {"ms_per_traversal": statistics.median(ts), "gteps": edges / (sum(ts) / 1e3) / 1e9,
+            "vs_32bit_ids": t32_ms / statistics.median(ts)}
+
+
 def rmat26_leg(args, grx, torch, flush, stream, dev, peak, peak_kind, with_cpu):
     """R-MAT scale 26 (int64 offsets, generated on the device): direction-
     optimising BFS from the 16 seeded sources (the hot path's roofline target),
@@ -637,6 +667,9 @@ def rmat26_leg(args, grx, torch, flush, stream, dev, peak, peak_kind, with_cpu):
     out["pagerank"] = {"ms": ts, "iters": 20, "ms_per_iter": statistics.median(ts) / 20,
                        "roofline_frac": pr_bytes(nv, ne, 8, 20) / (statistics.median(ts) / 1e3) / 1e9 / peak}
     del r
+    # 64-bit vertex ids (NEXT-3): the same sources on graph_load_csr64 / bfs64
+    e16 = sum(m["per_src"][s]["edges"] for s in srcs)
+    out["bfs64"] = bfs64_leg(grx, torch, ro, col, srcs, e16, knobs, flush, stream, m["traversal_ms_median"])
     if with_cpu:
         col_h = col.cpu().numpy()
         e_cpu, s_cpu, used = run_oracle_bfs_sample(ro_h, col_h, srcs, args.cpu_budget26)

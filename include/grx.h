@@ -244,6 +244,32 @@ grx_status pagerank(grx_graph *g, float damping, int iters, float *rank_out, voi
  * call.  Results agree within the FP32 tolerance either way. */
 grx_status grx_pagerank_block(grx_graph *g, int shift);
 
+/* ---- 64-bit vertex ids (graphs past 2^31 vertices) --------------------------
+ * Sec. 6.2 / Sec. 7: graphs too large for 32-bit vertex ids use 64-bit ids,
+ * at about half the throughput (Table 5).  graph_load_csr64 keeps every id,
+ * offset and count 64-bit, for any graph size (a small graph loaded this way
+ * exercises the same path); bfs64 traverses such a graph.  The other
+ * primitives refuse these graphs with GRX_EINVAL.
+ *
+ * graph_load_csr64 -- as graph_load_csr, with int64 row_offsets[nv+1] and
+ *   int64 col_indices[ne]; nv < 2^42; no weights.  flags: GRX_HOST_PTRS or
+ *   GRX_DEVICE_PTRS, optionally GRX_VALIDATE (offsets, column range, sorted
+ *   rows, no self-loops, symmetry; synchronises `stream`).  The library
+ *   copies the arrays.  grx_graph_info reports nv; graph_free frees it. */
+grx_status graph_load_csr64(grx_ctx *ctx, int64_t nv, int64_t ne, const int64_t *row_offsets,
+                            const int64_t *col_indices, int flags, void *stream, grx_graph **out);
+
+/* bfs64 -- Algorithm 1 / 2 (direction-optimising with opts->direction AUTO,
+ * the Sec. 6.1 rule with alpha / beta / exact_fv) on a graph_load_csr64
+ * graph.  depth_out: device int32[nv], hop distance, -1 if unreached.
+ * parent_out: NULL or device int64[nv] (src at src, -1 unreached, else a
+ * neighbour one level closer).  Persistent loop only, no collect_stats
+ * (GRX_EINVAL otherwise); a graph with 32-bit ids -> GRX_EINVAL (use bfs).
+ * A push level with more than 2^24 rows of over 1,024 edges sets GRX_ERANGE
+ * status.  Uses about 40 bytes of workspace per vertex (first use). */
+grx_status bfs64(grx_graph *g, int64_t src, int32_t *depth_out, int64_t *parent_out,
+                 const grx_opts *opts, void *stream);
+
 /* ---- allocation-free BFS ---------------------------------------------------
  * bfs_noalloc -- the same traversal as bfs(), for callers that cannot allocate
  * device memory (a host framework that owns the GPU's memory pool and forbids

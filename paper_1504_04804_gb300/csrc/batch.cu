@@ -583,6 +583,7 @@ grx_status batch_step_typed(grx_batch *b, int steps) {
 
 extern "C" grx_status grx_batch_footprint(const grx_graph *g, int kind, size_t *bytes_out) {
     if (!g || !bytes_out) return grx_fail(GRX_EINVAL, "grx_batch_footprint: NULL argument");
+    if (g->vid64) return grx_fail(GRX_EINVAL, "grx_batch_footprint: 64-bit vertex ids are served by bfs64 only");
     if (kind != GRX_KIND_BFS && kind != GRX_KIND_SSSP)
         return grx_fail(GRX_EINVAL, "grx_batch_footprint: bad kind %d", kind);
     *bytes_out = batch_bytes(g, kind);
@@ -592,6 +593,7 @@ extern "C" grx_status grx_batch_footprint(const grx_graph *g, int kind, size_t *
 extern "C" grx_status grx_batch_open(grx_graph *g, int kind, void *stream, grx_batch **out) {
     if (!g || !out) return grx_fail(GRX_EINVAL, "grx_batch_open: NULL argument");
     *out = nullptr;
+    if (g->vid64) return grx_fail(GRX_EINVAL, "grx_batch_open: 64-bit vertex ids are served by bfs64 only");
     if (kind != GRX_KIND_BFS && kind != GRX_KIND_SSSP)
         return grx_fail(GRX_EINVAL, "grx_batch_open: bad kind %d", kind);
     if (kind == GRX_KIND_SSSP && !g->w) return grx_fail(GRX_EINVAL, "grx_batch_open: SSSP needs weights");

@@ -302,7 +302,7 @@ extern "C" grx_status graph_free(grx_graph *g) {
 
 extern "C" grx_status grx_graph_info(const grx_graph *g, int64_t *nv, int64_t *ne) {
     if (!g) return grx_fail(GRX_EINVAL, "grx_graph_info: NULL graph");
-    if (nv) *nv = g->nv;
+    if (nv) *nv = g->vid64 ? g->nv64 : g->nv;
     if (ne) *ne = g->ne;
     return GRX_OK;
 }
@@ -366,6 +366,7 @@ static size_t workspace_new_bytes(const grx_graph *g, bool multi) {
 
 extern "C" grx_status grx_multi_footprint(const grx_graph *g, int kind, size_t *bytes_out) {
     if (!g || !bytes_out) return grx_fail(GRX_EINVAL, "grx_multi_footprint: NULL argument");
+    if (g->vid64) return grx_fail(GRX_EINVAL, "grx_multi_footprint: 64-bit vertex ids are served by bfs64 only");
     if (kind != GRX_KIND_BFS && kind != GRX_KIND_SSSP)
         return grx_fail(GRX_EINVAL, "grx_multi_footprint: bad kind %d", kind);
     *bytes_out = workspace_new_bytes(g, true) +
@@ -377,7 +378,7 @@ extern "C" grx_status grx_graph_status(grx_graph *g, void *stream) {
     if (!g) return grx_fail(GRX_EINVAL, "grx_graph_status: NULL graph");
     cudaStream_t s = (cudaStream_t)stream;
     GRX_CUDA(cudaStreamSynchronize(s));
-    if (!g->ws_ready) return GRX_OK;
+    if (!g->ws_ready && !g->ws64_ready) return GRX_OK;
     int st = 0;
     GRX_CUDA(cudaMemcpy(&st, &g->ctl->status, sizeof(int), cudaMemcpyDeviceToHost));
     if (st != 0) {
@@ -419,6 +420,9 @@ extern "C" grx_status grx_last_stats(grx_graph *g, void *stream, grx_trav_stats 
 // ---------------------------------------------------------------------------
 static grx_status check_graph(grx_graph *g, const char *who) {
     if (!g) return grx_fail(GRX_EINVAL, "%s: NULL graph", who);
+    if (g->vid64)
+        return grx_fail(GRX_EINVAL, "%s: the graph has 64-bit vertex ids (graph_load_csr64); bfs64 "
+                                    "traverses it", who);
     return GRX_OK;
 }
 

@@ -137,6 +137,14 @@ struct grx_graph {
     // CUDA-graph level loop of bfs (GRX_LOOP_GRAPH), per parent flag
     cudaGraphExec_t bfs_gexec[2];
     void *bfs_gargs;                 // device copy of the call's arguments
+    // 64-bit vertex ids (graph_load_csr64): columns, frontier queues and
+    // long-row lists of bfs64; nv64 is the vertex count (nv is -1 past 2^31)
+    int vid64;
+    int64_t nv64;
+    int64_t *col64;
+    int64_t *q64[2];
+    int64_t *lr64[3];
+    int ws64_ready;
     // bookkeeping for frees
     struct Alloc { void *p; size_t n; } allocs[96];
     int nallocs;

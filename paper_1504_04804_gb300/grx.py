@@ -91,6 +91,8 @@ SIGNATURES = [
     ("grx_batch_poll", _I, [_P, _P]),
     ("grx_batch_footprint", _I, [_P, _I, _P]),
     ("grx_multi_footprint", _I, [_P, _I, _P]),
+    ("graph_load_csr64", _I, [_P, _I64, _I64, _P, _P, _I, _P, _P]),
+    ("bfs64", _I, [_P, _I64, _P, _P, _P, _P]),
     ("grx_rmat_edges", _I, [_I, _I64, _U64, _U64, _U64, _U64, _P, _P, _P]),
     ("grx_edge_weights", _I, [_I64, _I64, _P, _P, ctypes.c_uint32, _U64, _P, _P]),
     ("grx_grid_edges", _I, [_I64, _I64, _U64, _U64, _P, _P, _P, _P]),
@@ -250,6 +252,38 @@ def graph_load_csr(row_offsets, col_indices, weights=None, validate: bool = Fals
 
 def graph_free(g: Graph):
     g.free()
+
+
+def graph_load_csr64(row_offsets, col_indices, validate: bool = False, stream=None, name: str = "") -> Graph:
+    """Copy a symmetric CSR with 64-bit vertex ids (int64 row_offsets [nv+1] and
+    col_indices [ne], numpy arrays or torch tensors, host or device) to the
+    GPU; only bfs64 traverses it."""
+    ctx = _ctx()
+    ro = _as_contig(row_offsets, np.int64, torch.int64)
+    col = _as_contig(col_indices, np.int64, torch.int64)
+    nv, ne = ro.numel() - 1, col.numel()
+    if ro.is_cuda != col.is_cuda:
+        raise ValueError("row_offsets and col_indices must both be on the host or both on the GPU")
+    flags = (GRX_DEVICE_PTRS if ro.is_cuda else GRX_HOST_PTRS) | (GRX_VALIDATE if validate else 0)
+    h = ctypes.c_void_p()
+    _check(lib().graph_load_csr64(ctx.handle, nv, ne, ro.data_ptr(), col.data_ptr() if ne else None,
+                                  flags, _stream_ptr(stream), ctypes.byref(h)), "graph_load_csr64")
+    if not ro.is_cuda:
+        torch.cuda.current_stream().synchronize() if stream is None else torch.cuda.synchronize()
+    return Graph(h, nv, ne, ctx.device, False, name)
+
+
+def bfs64(g: Graph, src: int, depth_out=None, parent_out=None, opts: grx_opts | None = None,
+          stream=None, parent: bool = False):
+    """Depths (int32 [nv], -1 = unreached) on a graph_load_csr64 graph; with
+    parent=True also int64 parents."""
+    d = _out(depth_out, g.nv, torch.int32, g.device)
+    p = None
+    if parent or parent_out is not None:
+        p = _out(parent_out, g.nv, torch.int64, g.device)
+    _check(lib().bfs64(g.handle, int(src), d.data_ptr(), p.data_ptr() if p is not None else None,
+                       ctypes.byref(opts) if opts is not None else None, _stream_ptr(stream)), "bfs64")
+    return (d, p) if p is not None else d
 
 
 def load(graph: "_inputs.Graph", validate: bool = False, stream=None, offsets64: bool = False) -> Graph:

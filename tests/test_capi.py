@@ -105,3 +105,11 @@ def _header_define(name, raw=False):
         if m:
             return m.group(1).strip() if raw else int(m.group(1))
     raise KeyError(name)
+
+
+def test_64bit_vertex_id_entry_points_check_arguments_without_gpu():
+    lib = grx.lib()
+    out = ctypes.c_void_p()
+    assert lib.graph_load_csr64(None, 4, 0, None, None, 0, None, ctypes.byref(out)) == grx.GRX_EINVAL
+    assert lib.bfs64(None, 0, None, None, None, None) == grx.GRX_EINVAL
+    assert b"NULL graph" in lib.grx_last_error()

@@ -157,7 +157,8 @@ def test_rmat26_dobfs_multi_source_and_pagerank():
     """R-MAT scale 26 with int64 offsets, as the benchmark loads it: one
     DOBFS source and two of the 64 multi-source lanes bit-exact against the
     oracle, every lane against the BFS invariants on host threads, and nine
-    lanes against single-source BFS on the GPU; PageRank after 20 iterations
+    lanes against single-source BFS on the GPU; the DOBFS source again with
+    64-bit vertex ids (bfs64) equal to it; PageRank after 20 iterations
     against the oracle's FP64 20-iteration result at every vertex (max
     relative error <= 1e-5; the oracle runs on a host thread meanwhile)."""
     if not torch.cuda.is_available():
@@ -184,6 +185,13 @@ def test_rmat26_dobfs_multi_source_and_pagerank():
         # every lane against the BFS invariants (multithreaded host checker)
         assert check_lanes_parallel(roh, colh, lanes, lambda b: d[b].cpu().numpy()) == [0] * 64
         del d
+        # the same traversal with 64-bit vertex ids (every id, offset and count int64)
+        g64 = grx.graph_load_csr64(ro.to(torch.int64), col.to(torch.int64))
+        assert torch.equal(grx.bfs64(g64, src), grx.bfs(g, src))
+        grx.graph_status(g64)
+        g64.free()
+        del g64
+        torch.cuda.empty_cache()
         r20 = grx.pagerank(g, 0.85, 20).cpu().numpy()
         grx.graph_status(g)
         assert abs(r20.astype(np.float64).sum() - 1.0) < 1e-3

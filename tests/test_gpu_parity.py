@@ -563,3 +563,56 @@ def test_bc_multi_isolated_source_lane_and_sssp_zero_weights(grx, loaded):
         want = oracle.sssp(h.row_offsets, h.col_indices, h.weights, s)
         for delta in (0, 1, 2):
             assert np.array_equal(grx.as_uint32(grx.sssp(dh, s, opts=grx.opts(sssp_delta=delta))), want), delta
+
+
+# ---- 64-bit vertex ids (graph_load_csr64 + bfs64)
+
+@pytest.fixture(scope="module")
+def loaded64(grx):
+    return {name: grx.graph_load_csr64(g.row_offsets.astype(np.int64), g.col_indices.astype(np.int64),
+                                       validate=True) for name, g in GRAPHS.items()}
+
+
+@pytest.mark.parametrize("name", list(GRAPHS))
+@pytest.mark.parametrize("mode", list(MODES))
+def test_bfs64_matches_oracle(grx, loaded64, name, mode):
+    """Every id, offset and count 64-bit (forced on small graphs): depths
+    bit-exact, int64 parents accepted by the oracle's checker; the star's hub
+    row (5,000 edges) goes through the long-row phase."""
+    g, dg = GRAPHS[name], loaded64[name]
+    srcs = _sources(g, 4, seed=2) + ([0] if name == "star" else [])
+    for s in srcs:
+        d, p = grx.bfs64(dg, s, parent=True, opts=grx.opts(direction=MODES[mode]))
+        want = oracle.bfs(g.row_offsets, g.col_indices, s)
+        got = d.cpu().numpy()
+        assert np.array_equal(got, want), (name, mode, s)
+        ph = p.cpu().numpy()
+        assert ph.max() < g.nv
+        assert oracle.check_bfs(g.row_offsets, g.col_indices, s, got, ph.astype(np.int32)) == 0
+    grx.graph_status(dg)
+
+
+def test_bfs64_switch_parameters_and_union(grx):
+    pairs = list(itertools.combinations(range(6), 2))
+    edges = []
+    for mask in range(1 << len(pairs)):
+        base = 6 * mask
+        edges += [(base + a, base + b) for i, (a, b) in enumerate(pairs) if mask >> i & 1]
+    u = inputs.csr_from_edges(6 << len(pairs), edges)
+    du = grx.graph_load_csr64(u.row_offsets, u.col_indices.astype(np.int64))
+    for s in (6 * 32767, 6 * 12345 + 3, 6 * 5 + 1):
+        want = oracle.bfs(u.row_offsets, u.col_indices, s)
+        for kw in ({}, {"alpha": 1e-6, "beta": 1.0, "exact_fv": 1}, {"alpha": 1e3}, {"direction": 2}):
+            assert np.array_equal(grx.bfs64(du, s, opts=grx.opts(**kw)).cpu().numpy(), want), (s, kw)
+
+
+def test_64bit_graphs_are_refused_by_the_other_primitives(grx, loaded64):
+    dg = loaded64["rmat10"]
+    for fn in (lambda: grx.bfs(dg, 1), lambda: grx.cc(dg), lambda: grx.pagerank(dg, 0.85, 5),
+               lambda: grx.bfs_multi(dg, [1, 2]), lambda: grx.multi_footprint(dg, 0)):
+        with pytest.raises(grx.GrxError) as e:
+            fn()
+        assert e.value.status == grx.GRX_EINVAL
+    # and a 32-bit graph is refused by bfs64
+    with pytest.raises(grx.GrxError):
+        grx.bfs64(grx.load(GRAPHS["rmat10"]), 1)
