@@ -28,7 +28,10 @@ constexpr int PR_ITEMS = 9;                  // odd: conflict-free strided smem 
 constexpr int PR_TILE = PR_BLOCK * PR_ITEMS;
 
 struct PrSmem {
-    float acc[PR_TILE + 2];
+    union alignas(16) {
+        float acc[PR_TILE + 2];
+        int32_t colt[PR_TILE];         // the tile's columns, staged before the gathers
+    };
     uint32_t qe[PR_TILE + 2];
     int32_t u[PR_TILE + 2];
     uint16_t rid[PR_TILE];
@@ -105,14 +108,29 @@ __global__ void __launch_bounds__(PR_BLOCK) k_pr_iter(
     const uint64_t e1 = min((uint64_t)ne, e0 + PR_TILE);
     const int len = (int)(e1 - e0);
     const int t0 = threadIdx.x * PR_ITEMS;
-    // the gathers need no row: all of a thread's loads go out first
+    // The tile's columns arrive in shared memory by coalesced 16-byte loads
+    // (a tile starts on a 16-byte boundary when the column array does:
+    // PR_TILE * 4 is a multiple of 16; the last tile's tail past its last
+    // full vector, or a column array an outside allocator left unaligned, is
+    // read word by word), then each thread takes its PR_ITEMS consecutive
+    // columns from there (odd stride: conflict-free) and issues all its
+    // gathers at once.
+    {
+        const int nvec = ((uintptr_t)col & 15u) == 0 ? len >> 2 : 0;
+        const int4 *src = reinterpret_cast<const int4 *>(col + e0);
+        int4 *dst = reinterpret_cast<int4 *>(sm.colt);
+        for (int i = threadIdx.x; i < nvec; i += PR_BLOCK) dst[i] = __ldg(src + i);
+        for (int i = (nvec << 2) + threadIdx.x; i < len; i += PR_BLOCK) sm.colt[i] = __ldg(col + e0 + i);
+    }
+    const int2 tr = __ldg(tiles + tile);
+    __syncthreads();
     int32_t u[PR_ITEMS];
 #pragma unroll
-    for (int k = 0; k < PR_ITEMS; ++k) u[k] = t0 + k < len ? __ldg(col + e0 + t0 + k) : -1;
+    for (int k = 0; k < PR_ITEMS; ++k) u[k] = t0 + k < len ? sm.colt[t0 + k] : -1;
     float g[PR_ITEMS];
 #pragma unroll
     for (int k = 0; k < PR_ITEMS; ++k) g[k] = u[k] >= 0 ? __ldg(c_in + u[k]) : 0.f;
-    const int2 tr = __ldg(tiles + tile);
+    __syncthreads();                   // colt is reused as the row accumulators below
     const int64_t i0 = tr.x;
     const int n = tr.y;
     if (threadIdx.x == 0) fix[tile] = -1;
