@@ -14,9 +14,10 @@
 //    Three of each rotate (slot L % 3).
 //  * Push with a small frontier (queue push): advance and filter are fused
 //    (Sec. 6.3).  The frontier's edges are cut into equal warp tiles (the
-//    degree prefix needs no scan pass); each lane takes PUSH_ITEMS
-//    consecutive edges and keeps their loads, bitmap probes and atomics in
-//    flight together.  The visited bitmap is the filter (test, then
+//    degree prefix needs no scan pass); each lane takes PUSH_ITEMS edges of
+//    the tile, item k at position k*32 + lane, so each of the warp's column
+//    loads reads one contiguous run, and keeps their loads, bitmap probes and
+//    atomics in flight together.  The visited bitmap is the filter (test, then
 //    atomicOr; the winner labels the vertex and appends it with one
 //    warp-aggregated atomic).
 //  * Push with a large frontier (bitmap push, 2 phases): the same tiles mark
@@ -261,8 +262,9 @@ __device__ LevelState next_state(const BfsArgs<OffT> &a, const LevelState &st, b
 // Loads warp tile `tile` of the frontier's edge sequence: the frontier
 // elements that start before the tile's end go to shared memory (i0 = the
 // element holding the tile's first edge), then every lane takes PUSH_ITEMS
-// consecutive edges: destination v[k], source u[k] (when WANT_U), valid
-// bits.  Returns the element holding the next tile's first edge.
+// edges of the tile, item k at position k*32 + lane (a warp's column loads
+// are contiguous): destination v[k], source u[k] (when WANT_U), valid bits.
+// Returns the element holding the next tile's first edge.
 template <typename OffT, bool WANT_U>
 __device__ __forceinline__ int64_t push_tile(const BfsArgs<OffT> &a, const int32_t *Qv,
                                              const uint32_t *Qe, const OffT *Qr, int64_t q,
@@ -297,12 +299,11 @@ __device__ __forceinline__ int64_t push_tile(const BfsArgs<OffT> &a, const int32
     __syncwarp();
     const uint32_t next_start = w.qe[n];
     int row[PUSH_ITEMS];
-    warp_tile_rows8(w.rid, w.qe, (uint32_t)e0, n, row);
-    const uint32_t t0 = (uint32_t)e0 + lane * PUSH_ITEMS;
+    warp_tile_rows8_strided(w.rid, w.qe, (uint32_t)e0, n, row);
     valid = 0;
 #pragma unroll
     for (int k = 0; k < PUSH_ITEMS; ++k) {
-        const uint32_t e = t0 + k;
+        const uint32_t e = (uint32_t)e0 + (uint32_t)k * 32 + lane;
         const int j = row[k];
         const bool ok = e < e1;
         v[k] = ok ? __ldg(a.col + w.rs[j] + (OffT)(e - w.qe[j])) : 0;
@@ -655,12 +656,11 @@ __device__ __forceinline__ void heavy_run(const BfsArgs<OffT> &a, const uint32_t
         __syncwarp();
         const uint32_t steplen = min(total, (uint32_t)PULL_HSTEP);
         int hrow[PULL_HITEMS];
-        warp_tile_rows8(w.hrid, w.hofs, 0u, nh, hrow);
-        const uint32_t j0 = lane * PULL_HITEMS;
+        warp_tile_rows8_strided(w.hrid, w.hofs, 0u, nh, hrow);   // item k at position k*32 + lane
         int32_t uu[PULL_HITEMS];
 #pragma unroll
         for (int k = 0; k < PULL_HITEMS; ++k) {
-            const uint32_t j = j0 + k;
+            const uint32_t j = (uint32_t)k * 32 + lane;
             const int h = hrow[k];
             uu[k] = j < steplen ? __ldg(a.col + w.hb[h] + (OffT)(j - w.hofs[h])) : -1;
         }
@@ -669,8 +669,10 @@ __device__ __forceinline__ void heavy_run(const BfsArgs<OffT> &a, const uint32_t
             if (uu[k] >= 0 && ((__ldca(Fin + (uu[k] >> 5)) >> (uu[k] & 31)) & 1u))
                 w.hpar[hrow[k]] = uu[k];          // any hit is a valid parent
         }
-        if (STATS && j0 < steplen)
-            scanned_e += (unsigned long long)min((uint32_t)PULL_HITEMS, steplen - j0);
+        if (STATS) {
+#pragma unroll
+            for (int k = 0; k < PULL_HITEMS; ++k) scanned_e += (uint32_t)k * 32 + lane < steplen ? 1ull : 0ull;
+        }
         __syncwarp();
         // the step consumed the first steplen edges of the concatenation
 #pragma unroll

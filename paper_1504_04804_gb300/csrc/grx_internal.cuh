@@ -588,6 +588,25 @@ __device__ __forceinline__ void warp_tile_rows8(uint16_t *rid, const uint32_t *s
     __syncwarp();
 }
 
+// Rows of the positions k*32 + lane of a 256-position warp tile (inputs as
+// warp_tile_rows8).  With this assignment item k of the 32 lanes covers 32
+// consecutive positions, so a warp's column loads for item k read one
+// contiguous 128-byte run (and the sorted targets of a row sit side by side
+// across the lanes) instead of 32 runs 32 bytes apart.  rid ends up holding
+// the row of every position.
+__device__ __forceinline__ void warp_tile_rows8_strided(uint16_t *rid, const uint32_t *starts, uint32_t origin,
+                                                        int n, int (&row)[8]) {
+    warp_tile_rows8(rid, starts, origin, n, row);     // rows of positions lane*8 + k
+    const unsigned int lane = threadIdx.x & 31;
+    reinterpret_cast<uint4 *>(rid)[lane] =
+        make_uint4((uint32_t)row[0] | (uint32_t)row[1] << 16, (uint32_t)row[2] | (uint32_t)row[3] << 16,
+                   (uint32_t)row[4] | (uint32_t)row[5] << 16, (uint32_t)row[6] | (uint32_t)row[7] << 16);
+    __syncwarp();
+#pragma unroll
+    for (int k = 0; k < 8; ++k) row[k] = rid[k * 32 + lane];
+    __syncwarp();
+}
+
 template <typename T>
 __device__ __forceinline__ T warp_sum(T x) {
 #pragma unroll

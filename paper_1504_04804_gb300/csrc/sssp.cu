@@ -153,13 +153,12 @@ __device__ void relax_round(const SsspArgs<OffT> &a, const SsState &st, SsWarpSm
         __syncwarp();
         const uint32_t next_start = w.qe[n];
         int row[SS_ITEMS];
-        warp_tile_rows8(w.rid, w.qe, (uint32_t)e0, n, row);
-        const uint32_t t0 = (uint32_t)e0 + lane * SS_ITEMS;
+        warp_tile_rows8_strided(w.rid, w.qe, (uint32_t)e0, n, row);   // item k at position k*32 + lane
         int32_t v[SS_ITEMS];
         uint32_t wt[SS_ITEMS], du[SS_ITEMS];
 #pragma unroll
         for (int k = 0; k < SS_ITEMS; ++k) {
-            const uint32_t e = t0 + k;
+            const uint32_t e = (uint32_t)e0 + (uint32_t)k * 32 + lane;
             const int j = row[k];
             const bool ok = e < e1;
             const OffT idx = ok ? w.rs[j] + (OffT)(e - w.qe[j]) : (OffT)0;
