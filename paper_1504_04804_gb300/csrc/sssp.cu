@@ -9,7 +9,9 @@
 // queue slot carries the vertex, its row start and the exclusive prefix of the
 // frontier's degrees, so the frontier's edges are cut into equal warp tiles
 // (each warp a contiguous range, rows by a branch-free scatter + max-scan) and
-// each lane keeps a run of 8 edges' loads in flight.  Two kinds of rounds:
+// each lane keeps 8 edges' loads in flight, item k at tile position
+// k*32 + lane so the warp's column and weight loads are contiguous runs.  Two
+// kinds of rounds:
 //  * small rounds: an improving lane claims v with the atomic min's old value,
 //    a per-vertex round stamp keeps v once, and v is appended with one
 //    warp-aggregated atomic;
