@@ -76,25 +76,68 @@ __device__ __forceinline__ void block_tile_rows(uint16_t *rid, int *wmax, const 
     for (int k = 0; k < PR_ITEMS; ++k) row[k] = max(row[k], carry);
 }
 
-// Adds each item's value to its row's shared accumulator, one atomic per run
-// of equal rows (rows of a thread's items are non-decreasing).
+// Adds each item's value to its row's shared accumulator.  A thread's items
+// are consecutive positions and its rows non-decreasing, and a warp's threads
+// hold consecutive runs of positions, so a row's items within a warp sit in
+// consecutive lanes.  A row whose items all fall strictly inside one lane's
+// items (neither its first nor its last run) has that lane as its only writer:
+// a plain store.  Rows at lane boundaries are summed across the warp by a
+// segmented shuffle scan and added once per warp by the lane where they end
+// (a hub row filling a whole tile costs one shared atomic per warp instead of
+// one per thread).
 __device__ __forceinline__ void add_runs(float *acc, const int (&row)[PR_ITEMS], const float (&g)[PR_ITEMS],
                                          int valid) {
-    if (valid <= 0) return;
-    int cj = row[0];
-    float part = 0.f;
+    const unsigned int lane = threadIdx.x & 31;
+    int fk = -1, lk = -1;          // rows of the lane's first run (when it ends inside the lane) and last run
+    float fs = 0.f, ls = 0.f;
+    if (valid > 0) {
+        int cj = row[0];
+        float part = 0.f;
+        bool first = true;
 #pragma unroll
-    for (int k = 0; k < PR_ITEMS; ++k) {
-        if (k < valid) {
-            if (row[k] != cj) {
-                atomicAdd(&acc[cj], part);
-                part = 0.f;
-                cj = row[k];
+        for (int k = 0; k < PR_ITEMS; ++k) {
+            if (k < valid) {
+                if (row[k] != cj) {
+                    if (first) {
+                        fk = cj;
+                        fs = part;
+                        first = false;
+                    } else {
+                        acc[cj] = part;           // a row inside this lane's items
+                    }
+                    part = 0.f;
+                    cj = row[k];
+                }
+                part += g[k];
             }
-            part += g[k];
+        }
+        lk = cj;
+        ls = part;
+    }
+    // The last run continues the previous lane's last run when the lane has a
+    // single run of the same row; otherwise it starts a segment.
+    const int pk = __shfl_up_sync(GRX_FULL_MASK, lk, 1);
+    const bool prev_same = lane > 0 && pk == lk && lk >= 0;
+    float sum = ls;
+    int head = (fk >= 0 || !prev_same) ? 1 : 0;
+    // segmented inclusive scan of the last runs (Hillis-Steele with head flags)
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const float s2 = __shfl_up_sync(GRX_FULL_MASK, sum, o);
+        const int h2 = __shfl_up_sync(GRX_FULL_MASK, head, o);
+        if (lane >= (unsigned)o && !head) {
+            sum += s2;
+            head |= h2;
         }
     }
-    atomicAdd(&acc[cj], part);
+    // the previous lane's scanned last run, for this lane's first run
+    const float ps = __shfl_up_sync(GRX_FULL_MASK, sum, 1);
+    if (fk >= 0) atomicAdd(&acc[fk], fs + ((lane > 0 && pk == fk) ? ps : 0.f));
+    // a last run whose row the next lane does not continue ends here
+    const int nfk = __shfl_down_sync(GRX_FULL_MASK, fk, 1);
+    const int nlk = __shfl_down_sync(GRX_FULL_MASK, lk, 1);
+    const bool next_cont = lane < 31 && ((nfk >= 0 && nfk == lk) || (nfk < 0 && nlk == lk));
+    if (lk >= 0 && !next_cont) atomicAdd(&acc[lk], sum);
 }
 
 __global__ void __launch_bounds__(PR_BLOCK) k_pr_iter(
