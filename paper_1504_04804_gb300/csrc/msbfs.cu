@@ -467,6 +467,68 @@ __device__ __forceinline__ void ms_pull_finish(unsigned long long *seen, unsigne
 }
 
 // Pull, phase 1: one block per static tile of the active list's edges.
+// ORs each item's lane mask into its row's shared accumulator.  A thread's
+// items are consecutive positions with non-decreasing rows, and a warp's
+// threads hold consecutive runs of positions, so a row's items within a warp
+// sit in consecutive lanes.  A row strictly inside one lane's items is stored
+// by that lane alone; rows at lane boundaries are OR-ed across the warp by a
+// segmented shuffle scan and added once per warp by the lane where they end
+// (a hub row filling a tile costs one shared atomic per warp, not one per
+// thread).  All 32 lanes call; valid = the lane's item count (0..MS_PITEMS).
+__device__ __forceinline__ void or_runs(unsigned long long *acc, const int (&row)[MS_PITEMS],
+                                        const unsigned long long (&g)[MS_PITEMS], int valid) {
+    const unsigned int lane = threadIdx.x & 31;
+    int fk = -1, lk = -1;          // rows of the lane's first run (when it ends inside the lane) and last run
+    unsigned long long fs = 0ull, ls = 0ull;
+    if (valid > 0) {
+        int cj = row[0];
+        unsigned long long part = 0ull;
+        bool first = true;
+#pragma unroll
+        for (int k = 0; k < MS_PITEMS; ++k) {
+            if (k < valid) {
+                if (row[k] != cj) {
+                    if (first) {
+                        fk = cj;
+                        fs = part;
+                        first = false;
+                    } else if (part) {
+                        acc[cj] = part;           // a row inside this lane's items
+                    }
+                    part = 0ull;
+                    cj = row[k];
+                }
+                part |= g[k];
+            }
+        }
+        lk = cj;
+        ls = part;
+    }
+    const int pk = __shfl_up_sync(GRX_FULL_MASK, lk, 1);
+    const bool prev_same = lane > 0 && pk == lk && lk >= 0;
+    unsigned long long m = ls;
+    int head = (fk >= 0 || !prev_same) ? 1 : 0;
+    // segmented inclusive OR-scan of the last runs (Hillis-Steele with head flags)
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const unsigned long long m2 = __shfl_up_sync(GRX_FULL_MASK, m, o);
+        const int h2 = __shfl_up_sync(GRX_FULL_MASK, head, o);
+        if (lane >= (unsigned)o && !head) {
+            m |= m2;
+            head |= h2;
+        }
+    }
+    const unsigned long long pm = __shfl_up_sync(GRX_FULL_MASK, m, 1);
+    if (fk >= 0) {
+        const unsigned long long x = fs | ((lane > 0 && pk == fk) ? pm : 0ull);
+        if (x) atomicOr(&acc[fk], x);
+    }
+    const int nfk = __shfl_down_sync(GRX_FULL_MASK, fk, 1);
+    const int nlk = __shfl_down_sync(GRX_FULL_MASK, lk, 1);
+    const bool next_cont = lane < 31 && ((nfk >= 0 && nfk == lk) || (nfk < 0 && nlk == lk));
+    if (lk >= 0 && !next_cont && m) atomicOr(&acc[lk], m);
+}
+
 template <typename OffT, bool STATS>
 __device__ void ms_pull(const MsArgs<OffT> &a, const MsState &st, MsPullSmem &p, MsCounts &c) {
     const int L = st.L;
@@ -501,8 +563,14 @@ __device__ void ms_pull(const MsArgs<OffT> &a, const MsState &st, MsPullSmem &p,
         // every column and every gather in flight together; rows with every
         // lane seen gather nothing
         const int t0 = threadIdx.x * MS_PITEMS;
+        int rj[MS_PITEMS];
+        unsigned long long gv[MS_PITEMS];
+#pragma unroll
+        for (int k = 0; k < MS_PITEMS; ++k) {
+            rj[k] = 0;
+            gv[k] = 0ull;
+        }
         if (t0 < len) {
-            int rj[MS_PITEMS];
             int j = upper_index_smem(p.qe, n, (uint32_t)(e0 + t0));
 #pragma unroll
             for (int k = 0; k < MS_PITEMS; ++k) {
@@ -515,26 +583,14 @@ __device__ void ms_pull(const MsArgs<OffT> &a, const MsState &st, MsPullSmem &p,
 #pragma unroll
             for (int k = 0; k < MS_PITEMS; ++k)
                 u[k] = (t0 + k < len && p.miss[rj[k]]) ? __ldg(a.col + e0 + t0 + k) : -1;
-            unsigned long long gv[MS_PITEMS];
 #pragma unroll
             for (int k = 0; k < MS_PITEMS; ++k) gv[k] = u[k] >= 0 ? __ldca(cin + u[k]) : 0ull;
             if (STATS) {
 #pragma unroll
                 for (int k = 0; k < MS_PITEMS; ++k) c.gathered += u[k] >= 0 ? 1ull : 0ull;
             }
-            int cj = rj[0];
-            unsigned long long part = 0ull;
-#pragma unroll
-            for (int k = 0; k < MS_PITEMS; ++k) {
-                if (rj[k] != cj) {
-                    if (part) atomicOr(&p.acc[cj], part);
-                    part = 0ull;
-                    cj = rj[k];
-                }
-                part |= gv[k];
-            }
-            if (part) atomicOr(&p.acc[cj], part);
         }
+        or_runs(p.acc, rj, gv, t0 < len ? min(MS_PITEMS, len - t0) : 0);
         __syncthreads();
         int open = 0;
         for (int j = threadIdx.x; j < n; j += MS_BLOCK) {
