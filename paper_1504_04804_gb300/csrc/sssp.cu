@@ -34,6 +34,9 @@
 namespace {
 
 constexpr int SS_BLOCK = 256;
+#ifndef GRX_SS_MIN_BLOCKS
+#define GRX_SS_MIN_BLOCKS 3                         // resident blocks per SM (register cap)
+#endif
 constexpr int SS_WARPS = SS_BLOCK / 32;
 constexpr int SS_ITEMS = 8;
 constexpr int SS_WTILE = 32 * SS_ITEMS;
@@ -371,7 +374,7 @@ __device__ SsState ss_next(const SsspArgs<OffT> &a, const SsState &st, bool stat
 }
 
 template <typename OffT, bool STATS>
-__global__ void __launch_bounds__(SS_BLOCK, 3) k_sssp_persistent(SsspArgs<OffT> a) {
+__global__ void __launch_bounds__(SS_BLOCK, GRX_SS_MIN_BLOCKS) k_sssp_persistent(SsspArgs<OffT> a) {
     __shared__ SsState s_st;
     __shared__ SsWarpSmem<OffT> wsm[SS_WARPS];
     SsWarpSmem<OffT> &w = wsm[threadIdx.x >> 5];

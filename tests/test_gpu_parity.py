@@ -28,6 +28,17 @@ def grx():
     return g
 
 
+def _ragged_edges(nh):
+    edges, leaf = [], nh
+    for h in range(nh):
+        if h + 1 < nh:
+            edges.append((h, h + 1))
+        for _ in range(h + 1):
+            edges.append((h, leaf))
+            leaf += 1
+    return edges
+
+
 def _graphs():
     gs = {
         "rmat10": inputs.rmat_graph(10, 16, seed=10, wmax=64, weight_seed=110),
@@ -38,8 +49,12 @@ def _graphs():
         "star": inputs.csr_from_edges(5001, [(0, i) for i in range(1, 5001)]),
         "disconnected": inputs.csr_from_edges(
             40, [(1, 2), (2, 3), (3, 1), (5, 6), (10, 11), (11, 12), (12, 13), (30, 31)]),
+        # rows of every length from 1 to 600 (hub h owns a block of h + 1 leaves, the
+        # hubs chained): row boundaries fall at every offset of the per-thread,
+        # per-lane and per-warp edge runs of the tiled kernels
+        "ragged": inputs.csr_from_edges(600 + 600 * 601 // 2, _ragged_edges(600)),
     }
-    for name in ("path", "star", "disconnected"):
+    for name in ("path", "star", "disconnected", "ragged"):
         g = gs[name]
         rows = np.repeat(np.arange(g.nv), np.diff(g.row_offsets))
         lo = np.minimum(rows, g.col_indices).astype(np.uint64)
