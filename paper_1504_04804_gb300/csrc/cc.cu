@@ -67,13 +67,28 @@ __device__ __forceinline__ void hook(int32_t *label, int32_t u, int32_t v, TravC
     }
 }
 
+// Root of x during a compress phase: no hooking runs, so roots cannot change
+// and every parent a write replaces is replaced by the root itself; a stale
+// parent is still an ancestor.  Reads may therefore be served by L1 (the
+// grid barrier's acquire drops what earlier phases left there), which keeps
+// the labels of the few large components' roots, read at the end of most
+// chains, out of a single L2 slice.
+__device__ __forceinline__ int32_t find_root_ca(const int32_t *label, int32_t x) {
+    int32_t p = __ldca(label + x);
+    while (p != x) {
+        x = p;
+        p = __ldca(label + x);
+    }
+    return x;
+}
+
 // Every vertex points at its root.
 __device__ void compress(const CcArgs &a) {
     for (int64_t v = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; v < a.nv;
          v += (int64_t)gridDim.x * blockDim.x) {
         const int32_t p = __ldcg(a.label + v);
         if (p == v) continue;
-        const int32_t r = find_root(a.label, p);
+        const int32_t r = find_root_ca(a.label, p);
         if (r != p) a.label[v] = r;
     }
 }
