@@ -132,7 +132,12 @@ __device__ void hook_rest(const CcArgs &a, int32_t giant, unsigned long long &li
     for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < a.n_active;
          i += (int64_t)gridDim.x * blockDim.x) {
         const int32_t v = __ldg(a.active + i);
-        if (find_root(a.label, v) == giant) continue;
+        // Membership in the largest component through L1: a stale view only
+        // shows an earlier ancestor chain, and trees only merge, so a vertex
+        // seen under the giant root is in its component (its edges to other
+        // components are hooked from their side); a stale view that misses
+        // the root only costs this vertex's own hooks.
+        if (find_root_ca(a.label, v) == giant) continue;
         const uint32_t b = __ldg(a.aoff + i), e = __ldg(a.aoff + i + 1);
         for (uint32_t k = b + 2; k < e; ++k) hook(a.label, v, __ldg(a.col + k), a.ctl);
         linked += e > b + 2 ? e - b - 2 : 0u;
