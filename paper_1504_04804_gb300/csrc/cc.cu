@@ -52,7 +52,11 @@ __device__ __forceinline__ int32_t find_root(int32_t *label, int32_t x) {
 // Every failed attempt means some parent decreased, so the loop ends; the cap
 // only guards against a corrupted label array (then the status is set).
 __device__ __forceinline__ void hook(int32_t *label, int32_t u, int32_t v, TravCtl *ctl) {
-    int32_t p1 = __ldcg(label + u), p2 = __ldcg(label + v);
+    // The first parents may come from L1 (a hub's label is read by most of its
+    // neighbours' hooks): a stale parent is still an ancestor, and the
+    // compare-and-swap below reads the larger root's parent fresh before it
+    // writes, so a stale start only costs a retry.
+    int32_t p1 = __ldca(label + u), p2 = __ldca(label + v);
     for (int tries = 0; p1 != p2; ++tries) {
         if (tries > (1 << 24)) {
             grx_set_status(ctl, GRX_ETIMEOUT);
