@@ -58,3 +58,33 @@ def test_reference_arm_runs_on_rank_0_only(monkeypatch):
         steps = 1
         warmup = 0
     assert bench.reference_arm(Args()) == 0          # returns at once: no graph, no oracle
+
+
+def test_reference_arm_line_on_a_small_graph(monkeypatch, capsys):
+    """The reference arm on rank 0 (the CPU oracle on a scale-10 stand-in for
+    the workload): one JSON line with the arm's fields; a step runs one BFS
+    from each seeded source, or from the first k when the run would pass the
+    time cap (here forced down to a single source per step)."""
+    import json
+    sys.path.insert(0, ROOT)
+    import bench
+    monkeypatch.delenv("RANK", raising=False)
+    monkeypatch.delenv("WORLD_SIZE", raising=False)
+    monkeypatch.setitem(bench.RMAT_CONFIGS, "rmat22",
+                        dict(scale=10, edge_factor=16, seed=10, wmax=64, weight_seed=110))
+
+    class Args:
+        workload = "rmat22"
+        steps = 2
+        warmup = 1
+    assert bench.reference_arm(Args()) == 0
+    line = json.loads(capsys.readouterr().out.strip().splitlines()[-1])
+    assert line["impl"] == "reference" and line["unit"] == "GTEPS" and line["value"] > 0
+    assert line["cpu_baseline"]["kind"] == "oracle" and line["cpu_baseline"]["cores"] == 1
+    assert "16 of the 16 seeded sources per step" in line["cpu_baseline"]["sample"]
+    assert line["e2e"] == {"value": line["value"], "unit": "GTEPS", "h2d_bytes_per_step": 0,
+                           "d2h_bytes_per_step": 0}
+    monkeypatch.setattr(bench, "REF_TIME_CAP_S", 0.0)
+    assert bench.reference_arm(Args()) == 0
+    line = json.loads(capsys.readouterr().out.strip().splitlines()[-1])
+    assert "1 of the 16 seeded sources per step" in line["cpu_baseline"]["sample"]
