@@ -217,6 +217,61 @@ def test_pagerank_dangling_closed_form():
         assert abs(r[0] - (1 - b) / 2) < 1e-15 and r[0] == r[1]
 
 
+def test_pagerank_star_closed_form():
+    """A star: hub 0 with n leaves (degree 1 each), no dangling vertex.  By
+    symmetry every leaf holds the same rank l, and with N = n + 1 the update is
+    h' = (1-d)/N + d*n*l,  l' = (1-d)/N + d*h/n  from h = l = 1/N: a
+    two-variable recurrence evaluated here in exact rational arithmetic.  The
+    oracle sums the hub's n terms in FP64: relative error within a few
+    (n + iterations) units of 2^-53."""
+    from fractions import Fraction
+    d = Fraction(85, 100)
+    for n in (1, 7, 5000):
+        g = inputs.csr_from_edges(n + 1, [(0, i) for i in range(1, n + 1)])
+        N = n + 1
+        h = l = Fraction(1, N)
+        tol = 4 * (n + 20) * 2.0 ** -53
+        for k in range(1, 21):
+            h, l = (1 - d) / N + d * n * l, (1 - d) / N + d * h / n
+            if k in (1, 2, 20):
+                r = oracle.pagerank(g.row_offsets, g.col_indices, 0.85, k)
+                assert abs(r[0] - float(h)) <= tol * float(h), (n, k)
+                assert np.max(np.abs(r[1:] - float(l))) <= tol * float(l), (n, k)
+
+
+def _ragged_graph(nh):
+    """600 hubs in a chain, hub h owning h + 1 private leaves."""
+    edges, leaf = [], nh
+    for h in range(nh):
+        if h + 1 < nh:
+            edges.append((h, h + 1))
+        for _ in range(h + 1):
+            edges.append((h, leaf))
+            leaf += 1
+    return inputs.csr_from_edges(leaf, edges)
+
+
+def test_bfs_sssp_cc_ragged_closed_forms():
+    """The chained-hub graph of the GPU parity set (rows of every length from 1
+    to nh + 1): from hub s, hub h sits at |h - s| and its leaves one further;
+    from a leaf of hub h everything is one further than from h; unit weights
+    give the same distances; one component, labelled 0."""
+    nh = 60
+    g = _ragged_graph(nh)
+    owner = np.concatenate([np.arange(nh)] + [np.full(h + 1, h) for h in range(nh)])
+    is_leaf = np.arange(g.nv) >= nh
+    ones = np.ones(g.col_indices.shape[0], dtype=np.uint32)
+    for s in (0, 17, nh - 1):
+        want = np.abs(owner - s) + is_leaf
+        assert np.array_equal(oracle.bfs(g.row_offsets, g.col_indices, s), want)
+        assert np.array_equal(oracle.sssp(g.row_offsets, g.col_indices, ones, s), want.astype(np.uint32))
+    leaf_of_5 = nh + 5 * 6 // 2                 # first leaf of hub 5
+    want = np.abs(owner - 5) + is_leaf + 1
+    want[leaf_of_5] = 0
+    assert np.array_equal(oracle.bfs(g.row_offsets, g.col_indices, leaf_of_5), want)
+    assert np.all(oracle.cc(g.row_offsets, g.col_indices) == 0)
+
+
 def test_golden_fixtures():
     """Hand-derived values for small named graphs (see each fixture's header)."""
     for name in sorted(os.listdir(GOLDEN)):
