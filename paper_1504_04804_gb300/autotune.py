@@ -72,26 +72,21 @@ def _save(path, data):
     os.replace(tmp, path)
 
 
-_FLUSH = {}
-
-
 def _l2_flush(torch, device):
     """A 256 MiB device buffer (twice the GB300's L2); writing it before a
-    timed traversal evicts the graph, as the benchmark does."""
-    buf = _FLUSH.get(device)
-    if buf is None:
-        buf = _FLUSH[device] = torch.empty(256 << 20, dtype=torch.uint8, device=f"cuda:{device}")
-    return buf
+    timed traversal evicts the graph, as the benchmark does.  Held only for
+    the duration of one tuning call."""
+    return torch.empty(256 << 20, dtype=torch.uint8, device=f"cuda:{device}")
 
 
-def _time_config(grx, torch, g, sources, kw, reps):
+def _time_config(grx, torch, g, sources, kw, reps, flush):
     """Median over sources of the per-traversal kernel time (ms) and the sum
     over sources of the mean time; every timed traversal starts from a
-    flushed L2 (the benchmark's condition), timed alone with CUDA events."""
+    flushed L2 (the benchmark's condition, `flush` written first), timed alone
+    with CUDA events."""
     o = grx.opts(**kw)
     stream = torch.cuda.current_stream()
     depth = torch.empty(g.nv, dtype=torch.int32, device=f"cuda:{g.device}")
-    flush = _l2_flush(torch, g.device)
     evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
            for _ in range(len(sources) * reps)]
     i = 0
@@ -124,6 +119,7 @@ def tune_bfs(g, row_offsets, n_sources: int = 8, seed: int = 2, reps: int = 2,
             return dict(hit, cached=True)
     t0 = time.time()
     sources = [int(s) for s in inputs.pick_sources(row_offsets, n_sources, seed)]
+    flush = _l2_flush(torch, g.device)
     grids = (0, -1)          # full occupancy, half of it
     best = None
     tried = 0
@@ -134,7 +130,7 @@ def tune_bfs(g, row_offsets, n_sources: int = 8, seed: int = 2, reps: int = 2,
             if full is None:
                 continue
             kw["grid_blocks"] = max(1, full // 2)
-        med, tot = _time_config(grx, torch, g, sources, kw, reps)
+        med, tot = _time_config(grx, torch, g, sources, kw, reps, flush)
         tried += 1
         if best is None or tot < best[0]:
             best = (tot, kw, med)
@@ -144,7 +140,7 @@ def tune_bfs(g, row_offsets, n_sources: int = 8, seed: int = 2, reps: int = 2,
     base = dict(best[1])
     for pb in PUSH_BITMAPS[1:]:
         kw = dict(base, push_bitmap=pb)
-        med, tot = _time_config(grx, torch, g, sources, kw, reps)
+        med, tot = _time_config(grx, torch, g, sources, kw, reps, flush)
         tried += 1
         if tot < best[0]:
             best = (tot, kw, med)
